@@ -1,0 +1,371 @@
+"""Benchmark of the GB300 IFGF operator apply (one JSON line on rank 0).
+
+A step is one pass of the whole hot path over one synthetic input: the plan (Morton
+octree, interaction lists, relevant cones) and the apply (near field, leaf evaluation,
+propagation, interpolation, permutations), i.e. ifgf_plan_create + ifgf_apply +
+ifgf_plan_destroy on device-resident inputs.  The workload is the 64-wavelength
+Fibonacci sphere with N = 1,572,864 points and one complex density vector, mixed
+precision, orders (3,5,5).  Metric: IFGF matvecs expressed as N*nrhs points per second.
+
+Multi-GPU: the method is run as independent replicas (one full problem per rank, no
+collective); value = points of all ranks / max step time over ranks ("weak" scaling).
+
+--impl reference times the oracle (the FP64 direct sum of Eq. (1), C/OpenMP) on the
+host cores, on a bounded sample of the same workload's targets.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ifgf_inputs as W  # noqa: E402
+
+METRIC = "IFGF matvecs/sec (N*nrhs pts/s) at stated rel. error vs FP64 direct sum"
+UNIT = "pts/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32 flops per unit of work (counted from the arithmetic of the method's
+# steps, independent of how the kernels schedule it; derivation in the design doc):
+#   interpolant evaluation at one point, orders (3,5,5): separable contraction
+#   4*(75+15+3) = 372, Chebyshev recurrences 2*(1+3+3) = 14, local coordinates 6,
+#   squared distance 5, factor/ratio multiply-accumulate 18  -> 415
+FLOPS_INTERP_EVAL = 415
+#   coefficient generation per node: 4*(5+5+3) = 52
+FLOPS_DCT_NODE = 52
+#   leaf pair (analytic factor of one source at one node, accumulate): 35
+FLOPS_LEAF_PAIR = 35
+#   near-field pair (distance, Green function, accumulate): 22
+FLOPS_NEAR_PAIR = 22
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.070 GHz (maximum SM clock).
+SMS, LANES, MAX_SM_GHZ = 152, 128, 2.070
+PEAK_FP32_TFLOPS = SMS * LANES * 2 * MAX_SM_GHZ / 1e3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere64")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_flops(work: dict, ncone: dict, P: int) -> dict:
+    prop = sum(work["prop"].values()) * FLOPS_INTERP_EVAL
+    prop += sum(ncone[d] for d in ncone if d < max(ncone)) * P * FLOPS_DCT_NODE
+    interp = sum(work["interp"].values()) * (FLOPS_INTERP_EVAL + 10)
+    leaf = work["leaf_pairs"] * FLOPS_LEAF_PAIR + ncone[max(ncone)] * P * FLOPS_DCT_NODE
+    near = work["near_pairs"] * FLOPS_NEAR_PAIR
+    return {"prop": prop, "interp": interp, "leaf": leaf, "near": near}
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel source (its sha256 is recorded beside the figure)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2112_15198_gb300", "csrc", "apply.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    for ln in open(path):
+        f = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("apply_sha") == sha and "bytes_per_launch" in f:
+            return float(f["bytes_per_launch"])
+    return None
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    w = W.make(args.workload)
+    pts = w.points()
+    dens = w.densities()
+    threads = oracle.max_threads()
+    # bounded sample: enough targets for ~3 s of CPU work per step
+    probe = W.targets(w.n, 32, 999)
+    t0 = time.perf_counter()
+    oracle.direct_sum(pts, w.kappa, dens, probe)
+    per_target = (time.perf_counter() - t0) / len(probe)
+    m = int(max(16, min(w.n, 3.0 / per_target)))
+    tg = W.targets(w.n, m, w.seed + 200)
+    for _ in range(args.warmup):
+        oracle.direct_sum(pts, w.kappa, dens, tg[:16])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.direct_sum(pts, w.kappa, dens, tg)
+        times.append(time.perf_counter() - t0)
+    value = m * w.nrhs / statistics.median(times)
+    sample = f"direct sum of Eq. (1) at {m} of the {w.n} targets per step (FP64, OpenMP)"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_of(w, args.precision, None),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_of(w, precision, D):
+    return {"workload": f"{w.name}: Fibonacci sphere, unit diameter, {w.wavelengths:g} wavelengths "
+                        f"(kappa = 2 pi x {w.wavelengths:g}), N = {w.n}, nrhs = {w.nrhs}, densities iid U[-1,1]+iU[-1,1]",
+            "N": w.n, "kappa": w.kappa, "nrhs": w.nrhs, "orders": [3, 5, 5], "precision": precision,
+            "base_cones": [2, 4, 8], "tau": 0.5, "leaf_target": 64, "levels": D,
+            "step": "ifgf_plan_create + ifgf_apply + ifgf_plan_destroy (device-resident inputs)",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+
+    import paper_2112_15198_gb300 as ifgf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    ifgf.load()
+    w = W.make(args.workload)
+    pts = w.points()
+    cdt = torch.complex64 if args.precision == "mixed" else torch.complex128
+    dens_np = w.densities()
+    P_host = torch.from_numpy(pts).pin_memory()
+    A_host = torch.from_numpy(dens_np).to(cdt).pin_memory()
+    P = P_host.to(dev)
+    A = A_host.to(dev)
+    out = torch.empty_like(A)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan = ifgf.Plan(P, w.kappa, precision=args.precision, max_nrhs=w.nrhs)
+        plan.apply(A, out)
+        plan.destroy()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region -------------------------------------------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    ifgf.timing_enable(True)
+    ifgf.timing_collect()
+    launches0 = ifgf.launch_count()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    launches = ifgf.launch_count() - launches0
+    kt = ifgf.timing_collect()
+    ifgf.timing_enable(False)
+    clk = clocks.stop()
+    ms_step = total_ms / args.steps
+    if pg:
+        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * w.n * w.nrhs / (ms_step / 1e3)
+
+    # ---- apply-only throughput on a persistent plan (context) ------------------------
+    plan = ifgf.Plan(P, w.kappa, precision=args.precision, max_nrhs=w.nrhs)
+    for _ in range(2):
+        plan.apply(A, out)
+    torch.cuda.synchronize()
+    ap_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.apply(A, out)
+        e1.record(stream)
+        e1.synchronize()
+        ap_ms.append(e0.elapsed_time(e1))
+    work = plan.work()
+    ncone = dict(plan.ncone)
+    D = plan.D
+    status = plan.status()
+
+    # ---- end to end through the C ABI with host buffers ------------------------------
+    out_host = torch.empty(A.shape, dtype=cdt).pin_memory()
+    Pd = torch.empty_like(P)
+    Ad = torch.empty_like(A)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Pd.copy_(P_host, non_blocking=True)
+        Ad.copy_(A_host, non_blocking=True)
+        pl = ifgf.Plan(Pd, w.kappa, precision=args.precision, max_nrhs=w.nrhs)
+        pl.apply(Ad, out)
+        out_host.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        pl.destroy()
+        if it >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_step = statistics.mean(e2e_ms)
+    if pg:
+        t = torch.tensor([e2e_step], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    h2d = P_host.numel() * P_host.element_size() + A_host.numel() * A_host.element_size()
+    d2h = out_host.numel() * out_host.element_size()
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel ----------------------------------------------
+    flops = algorithmic_flops(work, ncone, 75)
+    kinds = {k: v for k, v in kt.items() if k in flops and v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    per_launch_flops = flops[dom] * args.steps / dom_n
+    achieved = per_launch_flops / (dom_ms / dom_n / 1e3) / 1e12
+    kernel_name = {"prop": "k_prop_f32", "interp": "k_interp_f32", "leaf": "k_leaf_f32", "near": "k_near_f32"}[dom]
+    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / PEAK_FP32_TFLOPS, "traffic": traffic_record(kernel_name), "kernel": kernel_name,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (derived, not measured)",
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+                "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()}}
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "config": config_of(w, args.precision, D),
+           "e2e": {"value": ws * w.n * w.nrhs / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+           "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+           "apply_only": {"value": w.n * w.nrhs / (statistics.median(ap_ms) / 1e3), "unit": UNIT,
+                          "ms_per_apply": statistics.median(ap_ms)},
+           "roofline": roofline, "clocks": clk, "device_status": status,
+           "work_per_apply": {"near_pairs": work["near_pairs"], "leaf_pairs": work["leaf_pairs"],
+                              "interp_evals": sum(work["interp"].values()), "prop_evals": sum(work["prop"].values()),
+                              "cones": sum(ncone.values())}}
+
+    if not args.no_cpu_baseline and ws == 1:
+        import oracle
+
+        oracle.build()
+        threads = oracle.max_threads()
+        probe = W.targets(w.n, 32, 999)
+        t0 = time.perf_counter()
+        oracle.direct_sum(pts, w.kappa, dens_np, probe)
+        per_target = (time.perf_counter() - t0) / len(probe)
+        m = int(max(16, min(w.n, args.cpu_seconds / per_target)))
+        tg = W.targets(w.n, m, w.seed + 200)
+        t0 = time.perf_counter()
+        exact = oracle.direct_sum(pts, w.kappa, dens_np, tg)
+        el = time.perf_counter() - t0
+        got = out.cpu().numpy().astype(np.complex128)[:, tg]
+        res["cpu_baseline"] = {"value": m * w.nrhs / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"FP64 direct sum of Eq. (1) at {m} of the {w.n} targets ({el:.1f} s)"}
+        res["rel_err_vs_direct_sum"] = {"value": oracle.rel_l2(got, exact), "targets": m}
+    print(json.dumps(res), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * ifgf.h -- C ABI of the GB300 IFGF operator-apply library.
+ *
+ * The library evaluates the discrete operator of Eq. (1) of "Massively Parallelized
+ * Interpolated Factored Green Function Method" (Bauinger & Bruno):
+ *
+ *     I(x_l) = sum_{m != l} a_m G(x_l, x_m),   G(x,y) = exp(i kappa |x-y|) / (4 pi |x-y|),
+ *
+ * over N surface points x_1..x_N (kappa = 0 gives the Laplace kernel 1/(4 pi r)), with the
+ * IFGF method of Sec. 2 of that paper: an octree of N-point boxes, box-centred cone
+ * segments, the factorisation G(x,x') = G(x,x_k) g_k(x,x') of Eq. (3), and the three
+ * functions LevelDEvaluations, Propagation and Interpolation (Algorithms 1-8), plus the
+ * level-D neighbour interactions ("LevelDSingularInteractions", Sec. 2).
+ *
+ * Conventions
+ *   - Every pointer named "device" must be CUDA device memory of the current device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Functions return an ifgf_status and never abort or throw; ifgf_last_error() gives a
+ *     thread-local text for the last failure of the calling thread.
+ *   - Complex numbers are interleaved (re, im) pairs: complex128 = 2 x double,
+ *     complex64 = 2 x float.
+ */
+#ifndef IFGF_H
+#define IFGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ifgf_plan_s* ifgf_plan;
+
+typedef enum {
+    IFGF_OK = 0,
+    IFGF_ERR_INVALID_ARG = 1, /* bad argument: see ifgf_plan_create / ifgf_apply */
+    IFGF_ERR_OOM = 2,         /* device allocation failed; nothing leaked */
+    IFGF_ERR_CUDA = 3,        /* a CUDA call failed; the text names it */
+    IFGF_ERR_TIMEOUT = 4,     /* a bounded device wait expired */
+    IFGF_ERR_INTERNAL = 5,    /* a device-side consistency check failed (e.g. cone lookup miss) */
+    IFGF_ERR_UNSUPPORTED = 6  /* valid request outside what this build supports */
+} ifgf_status;
+
+typedef enum {
+    IFGF_PREC_FP64 = 0,  /* every floating-point step in FP64 (complex128 in/out) */
+    IFGF_PREC_MIXED = 1  /* FP32 arithmetic; grid-relative coordinates and large phases
+                            kept exact or reduced in extended precision (complex64 in/out) */
+} ifgf_precision;
+
+/*
+ * Method parameters.  Defaults (ifgf_options_default): MIXED, base cone grid (2, 4, 8),
+ * tau = 0.5, leaf_target = 64, max_nrhs = 1.
+ *   base_cones  (n_s, n_theta, n_phi) of the cone grid of boxes of at most tau wavelengths;
+ *               the grid of a level whose box side H_d exceeds tau*2^(e-1) wavelengths is the
+ *               base grid doubled e times in all three directions (n_phi >= 4, even).
+ *   leaf_target when levels == 0, D is the smallest level >= 3 whose mean relevant-leaf
+ *               occupancy N / n_D is at most leaf_target.
+ *   max_nrhs    largest nrhs that ifgf_apply will accept (buffers are sized for it).
+ */
+typedef struct {
+    int32_t struct_size;   /* sizeof(ifgf_options) */
+    int32_t precision;     /* ifgf_precision */
+    int32_t base_cones[3];
+    int32_t leaf_target;
+    int32_t max_nrhs;
+    int32_t reserved;
+    double tau;
+} ifgf_options;
+
+void ifgf_options_default(ifgf_options* opt);
+
+/*
+ * Build a plan: the Morton octree of the points and its relevant boxes (Sec. 2; Morton
+ * order of Sec. 3.2.1), neighbour and cousin sets (Eq. (2)), the cone grids and the
+ * relevant cone segments of Eq. (4) for levels 3..D in the order of Sec. 3.2.1, and the
+ * apply buffers.  Runs on `stream` and returns after it has completed.
+ *
+ *   points   device, 3*N doubles, structure of arrays: x[0..N), y[0..N), z[0..N), in the
+ *            caller's order.  Read only; the plan keeps its own sorted copy.
+ *   N        number of points, 2 <= N < 2^31.
+ *   kappa    wavenumber, finite and >= 0.
+ *   orders   (P_s, P_theta, P_phi) interpolation orders, or NULL for (3, 5, 5).  This build
+ *            supports (3,5,5) and (5,7,7).
+ *   levels   number of octree levels D in [3, 21], or 0 to choose it from leaf_target.
+ *   opt      NULL for the defaults.
+ *   out_plan receives the plan; unchanged on failure.
+ *
+ * Errors: IFGF_ERR_INVALID_ARG for N out of range, a non-finite coordinate, kappa < 0 or
+ * non-finite, unsupported orders, levels outside {0} U [3, 21], all points coincident, or
+ * two points sharing all three coordinates (G is singular there); IFGF_ERR_UNSUPPORTED when
+ * a level's dense cone table would exceed the build's limit; IFGF_ERR_OOM, IFGF_ERR_CUDA.
+ */
+ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, const int32_t* orders,
+                             int32_t levels, const ifgf_options* opt, void* stream, ifgf_plan* out_plan);
+
+/*
+ * Apply the operator: out = I(a) (Algorithm 5 with the target- and cone-parallel loops of
+ * Algorithms 6-8, plus the level-D neighbour sums).  Asynchronous on `stream`; the plan
+ * owns its scratch, so one plan must not be applied concurrently on two streams.
+ *
+ *   densities device, [nrhs][N] complex128 (FP64 plan) or complex64 (MIXED plan), the
+ *             caller's point order.  Read only.
+ *   nrhs      1 <= nrhs <= opt.max_nrhs.
+ *   out       device, same layout and type as densities; overwritten.  Must not alias it.
+ *
+ * Device-side consistency failures (a cone lookup that misses) are recorded in the plan
+ * and returned by the next ifgf_plan_query(IFGF_Q_STATUS).
+ */
+ifgf_status ifgf_apply(ifgf_plan plan, const void* densities, int32_t nrhs, void* out, void* stream);
+
+/*
+ * Same as ifgf_apply, restricted to some contributions (for staged checks):
+ *   near        nonzero adds the level-D neighbour interactions;
+ *   level_mask  bit d adds the level-d cousin interpolations (all: -1).
+ */
+ifgf_status ifgf_apply_ex(ifgf_plan plan, const void* densities, int32_t nrhs, void* out, void* stream,
+                          int32_t near, int64_t level_mask);
+
+/* Release the plan and all its device memory (synchronous).  NULL is accepted. */
+ifgf_status ifgf_plan_destroy(ifgf_plan plan);
+
+/*
+ * Introspection (synchronous).  Copies the requested array into host_buf as int64 values
+ * when host_buf != NULL and *inout_count is large enough; always stores the element count
+ * in *inout_count.  `level` selects the octree level where the item is per level.
+ */
+enum {
+    IFGF_Q_PERM = 0,        /* [N] sorted position -> caller index */
+    IFGF_Q_KEYS = 1,        /* [N] sorted 60-bit level-21 Morton keys */
+    IFGF_Q_BOX_KEYS = 2,    /* [n_d] Morton keys of the relevant boxes */
+    IFGF_Q_BOX_START = 3,   /* [n_d + 1] first sorted point of each box */
+    IFGF_Q_BOX_PARENT = 4,  /* [n_d] parent box (level d-1), -1 at level 1 */
+    IFGF_Q_NBR_COUNT = 5,   /* [n_d] neighbour counts (levels >= 2) */
+    IFGF_Q_NBR_LIST = 6,    /* concatenated ascending neighbour lists */
+    IFGF_Q_COUS_COUNT = 7,  /* [n_d] cousin counts (levels >= 3) */
+    IFGF_Q_COUS_LIST = 8,   /* concatenated ascending cousin lists */
+    IFGF_Q_CONE_BOX = 9,    /* [c_d] box of each relevant cone, in cone order */
+    IFGF_Q_CONE_GAMMA = 10, /* [c_d] linear cone index (is*nt + it)*np + ip */
+    IFGF_Q_GRID = 11,       /* [3] (n_s, n_theta, n_phi) of level d */
+    IFGF_Q_INFO = 12,       /* [44] N, D, n_1..n_21, c_1..c_21 */
+    IFGF_Q_WORK = 13,       /* [4] near pairs, leaf pairs, level-d interpolations, level-d propagations */
+    IFGF_Q_STATUS = 14,     /* [1] sticky device status (ifgf_status) */
+    IFGF_Q_CHILD_START = 15 /* [n_d + 1] first child box in level d+1 */
+};
+ifgf_status ifgf_plan_query(ifgf_plan plan, int32_t what, int32_t level, int64_t* host_buf, int64_t* inout_count);
+
+/* Text of a status code, and the calling thread's last error detail. */
+const char* ifgf_status_string(ifgf_status s);
+const char* ifgf_last_error(void);
+
+/* Number of kernels this library has launched in this process (all plans). */
+int64_t ifgf_launch_count(void);
+
+/*
+ * Opt-in live timing of the hot kernels: while enabled, every launch of a timed kernel is
+ * bracketed by CUDA events on its own stream.  ifgf_timing_collect waits for the recorded
+ * events, writes per-kind totals (milliseconds, launch counts) into ms[6] / launches[6]
+ * (either may be NULL) and resets them.  Kinds: 0 permutations, 1 near field, 2 leaf
+ * evaluation, 3 propagation, 4 interpolation, 5 whole plan construction.
+ */
+void ifgf_timing_enable(int32_t on);
+ifgf_status ifgf_timing_collect(double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFGF_H */

@@ -1,0 +1,231 @@
+"""GB300 IFGF operator apply -- Python binding of the C ABI in ``include/ifgf.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libifgf_<arch>.so``.  There is no fallback: if the library is missing
+and cannot be built, importing the binding's functions raises.
+
+Device buffers are passed as torch CUDA tensors (or raw integer device
+pointers); torch supplies device memory and streams, nothing else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["IFGFError", "Plan", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q",
+           "PREC_FP64", "PREC_MIXED"]
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+
+class Q:
+    """Query codes of ifgf_plan_query."""
+
+    PERM, KEYS, BOX_KEYS, BOX_START, BOX_PARENT = 0, 1, 2, 3, 4
+    NBR_COUNT, NBR_LIST, COUS_COUNT, COUS_LIST = 5, 6, 7, 8
+    CONE_BOX, CONE_GAMMA, GRID, INFO, WORK, STATUS, CHILD_START = 9, 10, 11, 12, 13, 14, 15
+
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED"}
+
+
+class IFGFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("base_cones", ctypes.c_int32 * 3),
+        ("leaf_target", ctypes.c_int32),
+        ("max_nrhs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("tau", ctypes.c_double),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load (building first if needed and allowed) the CUDA library; raise if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"IFGF CUDA library not found at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.ifgf_options_default.argtypes = [ctypes.POINTER(Options)]
+        lib.ifgf_options_default.restype = None
+        lib.ifgf_plan_create.argtypes = [vp, i64, dbl, ctypes.POINTER(i32), i32, ctypes.POINTER(Options), vp,
+                                         ctypes.POINTER(vp)]
+        lib.ifgf_plan_create.restype = ctypes.c_int
+        lib.ifgf_apply.argtypes = [vp, vp, i32, vp, vp]
+        lib.ifgf_apply.restype = ctypes.c_int
+        lib.ifgf_apply_ex.argtypes = [vp, vp, i32, vp, vp, i32, i64]
+        lib.ifgf_apply_ex.restype = ctypes.c_int
+        lib.ifgf_plan_destroy.argtypes = [vp]
+        lib.ifgf_plan_destroy.restype = ctypes.c_int
+        lib.ifgf_plan_query.argtypes = [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.ifgf_plan_query.restype = ctypes.c_int
+        lib.ifgf_status_string.argtypes = [ctypes.c_int]
+        lib.ifgf_status_string.restype = ctypes.c_char_p
+        lib.ifgf_last_error.argtypes = []
+        lib.ifgf_last_error.restype = ctypes.c_char_p
+        lib.ifgf_launch_count.argtypes = []
+        lib.ifgf_launch_count.restype = i64
+        lib.ifgf_timing_enable.argtypes = [i32]
+        lib.ifgf_timing_enable.restype = None
+        lib.ifgf_timing_collect.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+        lib.ifgf_timing_collect.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(st: int):
+    if st != 0:
+        lib = load()
+        raise IFGFError(st, lib.ifgf_last_error().decode(errors="replace"))
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def launch_count() -> int:
+    return int(load().ifgf_launch_count())
+
+
+TIMING_KINDS = ("perm", "near", "leaf", "prop", "interp", "plan")
+
+
+def timing_enable(on: bool = True) -> None:
+    """Bracket every hot-kernel launch with CUDA events on its stream (live kernel timing)."""
+    load().ifgf_timing_enable(1 if on else 0)
+
+
+def timing_collect() -> dict:
+    """Wait for the recorded events; return {kind: (total ms, launches)} and reset."""
+    ms = (ctypes.c_double * 6)()
+    cnt = (ctypes.c_int64 * 6)()
+    _check(load().ifgf_timing_collect(ms, cnt))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(TIMING_KINDS)}
+
+
+class Plan:
+    """An IFGF plan over N points (ifgf_plan_create); apply() evaluates Eq. (1) for densities."""
+
+    def __init__(self, points, kappa: float, orders=(3, 5, 5), levels: int = 0, precision: str = "mixed",
+                 base_cones=(2, 4, 8), tau: float = 0.5, leaf_target: int = 64, max_nrhs: int = 1, stream=None,
+                 n: int | None = None):
+        lib = load()
+        self._lib = lib
+        opt = Options()
+        lib.ifgf_options_default(ctypes.byref(opt))
+        opt.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+        opt.base_cones[0], opt.base_cones[1], opt.base_cones[2] = (int(v) for v in base_cones)
+        opt.tau = float(tau)
+        opt.leaf_target = int(leaf_target)
+        opt.max_nrhs = int(max_nrhs)
+        if n is None:
+            shape = tuple(points.shape)
+            if len(shape) != 2 or shape[0] != 3:
+                raise ValueError("points must have shape (3, N)")
+            n = shape[1]
+        self.N = int(n)
+        self.precision = precision
+        self.max_nrhs = int(max_nrhs)
+        o = (ctypes.c_int32 * 3)(*(int(v) for v in orders))
+        h = ctypes.c_void_p()
+        _check(lib.ifgf_plan_create(_ptr(points), self.N, float(kappa), o, int(levels), ctypes.byref(opt),
+                                    _stream(stream), ctypes.byref(h)))
+        self._h = h
+        info = self.query(Q.INFO)
+        self.D = int(info[1])
+        self.nbox = {d: int(info[1 + d]) for d in range(1, self.D + 1)}
+        self.ncone = {d: int(info[22 + d]) for d in range(3, self.D + 1)}
+
+    def apply(self, dens, out, nrhs: int | None = None, stream=None, near: bool = True, level_mask: int = -1):
+        """out <- I(dens); dens/out are [nrhs][N] complex (complex64 for mixed, complex128 for fp64)."""
+        if nrhs is None:
+            nrhs = 1 if len(dens.shape) == 1 else int(dens.shape[0])
+        if near and level_mask == -1:
+            _check(self._lib.ifgf_apply(self._h, _ptr(dens), int(nrhs), _ptr(out), _stream(stream)))
+        else:
+            _check(self._lib.ifgf_apply_ex(self._h, _ptr(dens), int(nrhs), _ptr(out), _stream(stream),
+                                           1 if near else 0, int(level_mask)))
+        return out
+
+    def query(self, what: int, level: int = 0) -> np.ndarray:
+        cnt = ctypes.c_int64(0)
+        _check(self._lib.ifgf_plan_query(self._h, int(what), int(level), None, ctypes.byref(cnt)))
+        buf = np.zeros(max(cnt.value, 1), dtype=np.int64)
+        cnt2 = ctypes.c_int64(buf.shape[0])
+        _check(self._lib.ifgf_plan_query(self._h, int(what), int(level),
+                                         buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(cnt2)))
+        return buf[: cnt.value]
+
+    def status(self) -> int:
+        return int(self.query(Q.STATUS)[0])
+
+    def grid(self, level: int):
+        return tuple(int(v) for v in self.query(Q.GRID, level))
+
+    def work(self) -> dict:
+        """Exact work of one apply: near pairs, leaf pairs, per-level interpolations/propagations."""
+        res = {"interp": {}, "prop": {}}
+        for d in range(3, self.D + 1):
+            w = self.query(Q.WORK, d)
+            res["near_pairs"], res["leaf_pairs"] = int(w[0]), int(w[1])
+            res["interp"][d] = int(w[2])
+            res["prop"][d] = int(w[3])
+        return res
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _check(self._lib.ifgf_plan_destroy(h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()

@@ -1,0 +1,581 @@
+// Apply kernels of the IFGF operator (Algorithm 5 with the parallel loops of Algorithms 6-8)
+// and the level-D neighbour sums ("LevelDSingularInteractions", Sec. 2).
+//
+// Two arithmetic variants share the plan and its exact FP32 cone classification:
+//   mixed  FP32 arithmetic on grid-unit offsets (exact integer box-centre differences plus
+//          FP32 leaf offsets); the large centred-factor phases kappa |x - x_B| are split into
+//          a per-level FP64 table of (kappa |c_A - c_B|) mod 2 pi and a small FP32 correction;
+//          the analytic factor and the propagation ratio are written in cancellation-free
+//          forms whose phases stay below kappa h_d.
+//   fp64   every value in FP64 on physical coordinates.
+#include <cmath>
+
+#include "ifgf_internal.cuh"
+
+namespace ifgf {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---- permutations -----------------------------------------------------------------------
+template <class T>
+__global__ void k_perm_in(const T* __restrict__ a, const int32_t* __restrict__ perm, int64_t N, T* __restrict__ as) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t r = blockIdx.y;
+    as[r * N + i] = a[r * N + perm[i]];
+}
+
+template <class T>
+__global__ void k_perm_out(const T* __restrict__ Is, const int32_t* __restrict__ perm, int64_t N, T* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t r = blockIdx.y;
+    out[r * N + perm[i]] = Is[r * N + i];
+}
+
+// ---- near field --------------------------------------------------------------------------
+// I(x_l) = sum over the points x_m of the 27 neighbour leaves of leaf(x_l), m != l, of a_m G.
+__global__ void k_near_f32(int64_t N, const int32_t* __restrict__ pboxD, const int4* __restrict__ kD,
+                           const int32_t* __restrict__ startD, const int32_t* __restrict__ nnb,
+                           const int32_t* __restrict__ nb, const float4* __restrict__ off,
+                           const float2* __restrict__ as, float2* __restrict__ Is, float ku, float inv4piu) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t r = blockIdx.y;
+    const int l = pboxD[i];
+    const int4 kl = kD[l];
+    const float4 oi = off[i];
+    const float2* ar = as + r * N;
+    float2 acc = make_float2(0.f, 0.f);
+    const int cnt = nnb[l];
+    for (int t = 0; t < cnt; ++t) {
+        const int q = nb[(int64_t)l * kMaxNbr + t];
+        const int4 kq = kD[q];
+        const float bx = (float)(2 * (kl.x - kq.x)) + oi.x;
+        const float by = (float)(2 * (kl.y - kq.y)) + oi.y;
+        const float bz = (float)(2 * (kl.z - kq.z)) + oi.z;
+        const int j1 = startD[q + 1];
+        for (int j = startD[q]; j < j1; ++j) {
+            if (j == i) continue;
+            const float4 oj = __ldg(&off[j]);
+            const float vx = bx - oj.x, vy = by - oj.y, vz = bz - oj.z;
+            const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+            const float rinv = rsqrtf(r2);
+            const float2 e = cis_f32(ku * (r2 * rinv));
+            const float w = inv4piu * rinv;
+            const float2 aj = __ldg(&ar[j]);
+            const float2 g = make_float2(e.x * w, e.y * w);
+            acc = __ffma2_rn(make_float2(aj.x, aj.x), g, acc);
+            acc = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(g.y, g.x), acc);
+        }
+    }
+    Is[r * N + i] = acc;
+}
+
+__global__ void k_near_f64(int64_t N, const int32_t* __restrict__ pboxD, const int32_t* __restrict__ startD,
+                           const int32_t* __restrict__ nnb, const int32_t* __restrict__ nb,
+                           const double* __restrict__ Xs, const double2* __restrict__ as, double2* __restrict__ Is,
+                           double kappa) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t r = blockIdx.y;
+    const int l = pboxD[i];
+    const double xi = Xs[i], yi = Xs[N + i], zi = Xs[2 * N + i];
+    const double2* ar = as + r * N;
+    double2 acc = make_double2(0., 0.);
+    const double inv4pi = 0.079577471545947667884441881686257181;
+    for (int t = 0; t < nnb[l]; ++t) {
+        const int q = nb[(int64_t)l * kMaxNbr + t];
+        for (int j = startD[q]; j < startD[q + 1]; ++j) {
+            if (j == i) continue;
+            const double dx = xi - Xs[j], dy = yi - Xs[N + j], dz = zi - Xs[2 * N + j];
+            const double rr = sqrt(dx * dx + dy * dy + dz * dz);
+            double sn, cs;
+            sincos(kappa * rr, &sn, &cs);
+            const double w = inv4pi / rr;
+            acc = make_double2(acc.x + (ar[j].x * cs - ar[j].y * sn) * w, acc.y + (ar[j].x * sn + ar[j].y * cs) * w);
+        }
+    }
+    Is[r * N + i] = acc;
+}
+
+// ---- coefficient generation ("generate interpolant") -------------------------------------
+// Chebyshev coefficients of the P node values held in smem f (index (i*PT + j)*PP + k), by the
+// separable analysis matrices Ws | Wt | Wp; g is scratch of the same size.
+template <int PS, int PT, int PP, class T2, class R>
+__device__ __forceinline__ T2 cheb_coeffs_smem(T2* f, T2* g, const R* __restrict__ W, int n) {
+    constexpr int P = PS * PT * PP;
+    const R* Ws = W;
+    const R* Wt = W + PS * PS;
+    const R* Wp = Wt + PT * PT;
+    const int c = n % PP, b = (n / PP) % PT, a = n / (PP * PT);
+    if (n < P) {
+        T2 acc{};
+        const T2* row = f + (a * PT + b) * PP;
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const R w = Wp[c * PP + k];
+            acc.x += w * row[k].x;
+            acc.y += w * row[k].y;
+        }
+        g[n] = acc;
+    }
+    __syncthreads();
+    if (n < P) {
+        T2 acc{};
+#pragma unroll
+        for (int j = 0; j < PT; ++j) {
+            const R w = Wt[b * PT + j];
+            const T2 v = g[(a * PT + j) * PP + c];
+            acc.x += w * v.x;
+            acc.y += w * v.y;
+        }
+        f[n] = acc;
+    }
+    __syncthreads();
+    T2 out{};
+    if (n < P) {
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const R w = Ws[a * PS + i];
+            const T2 v = f[(i * PT + b) * PP + c];
+            out.x += w * v.x;
+            out.y += w * v.y;
+        }
+    }
+    return out;
+}
+
+// ---- LevelDEvaluations (Algorithm 6) ------------------------------------------------------
+// One block per relevant leaf cone, one thread per interpolation node y:
+//   F(y) = sum_{x' in B} a(x') g_k(y, x'),  g_k = G(y,x')/G(y,x_k)  (Eq. (3)),
+// with y = x_k + (h/s) yhat and u = (x' - x_k)/h:
+//   g_k = exp(i kappa h (s|u|^2 - 2 yhat.u) / (|yhat - s u| + 1)) / |yhat - s u|.
+template <int PS, int PT, int PP>
+__global__ void k_leaf_f32(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam, LevelGrid g,
+                           const int32_t* __restrict__ startD, const float4* __restrict__ off,
+                           const float2* __restrict__ as, int64_t N, float kh, float hinv,
+                           const float* __restrict__ W, float2* __restrict__ coef, int cstride, int nrhs) {
+    constexpr int P = PS * PT * PP;
+    __shared__ float2 f[P], tmp[P];
+    const int cone = blockIdx.x;
+    const int r = blockIdx.y;
+    const int n = threadIdx.x;
+    const int b = cone_box[cone];
+    if (n < P) {
+        const int gam = cone_gam[cone];
+        const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
+        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+        const float s = g.snode[is * PS + ia];
+        const float st = g.stn[it * PT + ib], ct = g.ctn[it * PT + ib];
+        const float yx = st * g.cpn[ip * PP + ic], yy = st * g.spn[ip * PP + ic], yz = ct;
+        const float2* ar = as + (int64_t)r * N;
+        float2 acc = make_float2(0.f, 0.f);
+        const int j1 = startD[b + 1];
+        for (int j = startD[b]; j < j1; ++j) {
+            const float4 o = __ldg(&off[j]);
+            const float ux = o.x * hinv, uy = o.y * hinv, uz = o.z * hinv;
+            const float wx = fmaf(-s, ux, yx), wy = fmaf(-s, uy, yy), wz = fmaf(-s, uz, yz);
+            const float q = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+            const float rq = rsqrtf(q);
+            const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+            const float yu = fmaf(yx, ux, fmaf(yy, uy, yz * uz));
+            const float num = fmaf(s, uu, -2.f * yu);
+            const float ph = kh * __fdividef(num, fmaf(q, rq, 1.f));
+            const float2 e = cis_f32(ph);
+            const float2 gk = make_float2(e.x * rq, e.y * rq);
+            const float2 aj = __ldg(&ar[j]);
+            acc = __ffma2_rn(make_float2(aj.x, aj.x), gk, acc);
+            acc = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(gk.y, gk.x), acc);
+        }
+        f[n] = acc;
+    }
+    __syncthreads();
+    const float2 c = cheb_coeffs_smem<PS, PT, PP>(f, tmp, W, n);
+    if (n < P) coef[((int64_t)cone * nrhs + r) * cstride + n] = c;
+}
+
+template <int PS, int PT, int PP>
+__global__ void k_leaf_f64(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam, LevelGrid g,
+                           const int32_t* __restrict__ startD, const int4* __restrict__ kD,
+                           const double* __restrict__ Xs, const double2* __restrict__ as, int64_t N, double kappa,
+                           double a0, double a1, double a2, double HD, const double* __restrict__ W,
+                           double2* __restrict__ coef, int cstride, int nrhs) {
+    constexpr int P = PS * PT * PP;
+    __shared__ double2 f[P], tmp[P];
+    const int cone = blockIdx.x;
+    const int r = blockIdx.y;
+    const int n = threadIdx.x;
+    const int b = cone_box[cone];
+    if (n < P) {
+        const int gam = cone_gam[cone];
+        const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
+        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+        const int4 k = kD[b];
+        const double xc = a0 + (k.x + 0.5) * HD, yc = a1 + (k.y + 0.5) * HD, zc = a2 + (k.z + 0.5) * HD;
+        const double s = g.snode64[is * PS + ia], th = g.tnode64[it * PT + ib], ph = g.pnode64[ip * PP + ic];
+        const double rr = g.h64 / s;
+        const double yx = xc + rr * sin(th) * cos(ph), yy = yc + rr * sin(th) * sin(ph), yz = zc + rr * cos(th);
+        const double rk = sqrt((yx - xc) * (yx - xc) + (yy - yc) * (yy - yc) + (yz - zc) * (yz - zc));
+        const double2* ar = as + (int64_t)r * N;
+        double2 acc = make_double2(0., 0.);
+        for (int j = startD[b]; j < startD[b + 1]; ++j) {
+            const double dx = yx - Xs[j], dy = yy - Xs[N + j], dz = yz - Xs[2 * N + j];
+            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+            double sn, cs;
+            sincos(kappa * (dist - rk), &sn, &cs);
+            const double w = rk / dist;
+            acc = make_double2(acc.x + (ar[j].x * cs - ar[j].y * sn) * w, acc.y + (ar[j].x * sn + ar[j].y * cs) * w);
+        }
+        f[n] = acc;
+    }
+    __syncthreads();
+    const double2 c = cheb_coeffs_smem<PS, PT, PP>(f, tmp, W, n);
+    if (n < P) coef[((int64_t)cone * nrhs + r) * cstride + n] = c;
+}
+
+// Node offset (grid units, FP32) of node n of cone gamma from the centre of its box: the same
+// correctly rounded products as the plan's activation, so the classification agrees with it.
+__device__ __forceinline__ float3 node_grid(const LevelGrid& gp, int Ps, int Pt, int Pp, int gam, int n) {
+    const int ip = gam % gp.np, it = (gam / gp.np) % gp.nt, is = gam / (gp.np * gp.nt);
+    const int c = n % Pp, b = (n / Pp) % Pt, a = n / (Pp * Pt);
+    const float rho = gp.rho[is * Ps + a];
+    const float st = gp.stn[it * Pt + b], ct = gp.ctn[it * Pt + b];
+    const float cp = gp.cpn[ip * Pp + c], sp = gp.spn[ip * Pp + c];
+    return make_float3(__fmul_rn(rho, __fmul_rn(st, cp)), __fmul_rn(rho, __fmul_rn(st, sp)), __fmul_rn(rho, ct));
+}
+
+// ---- Propagation(d) (Algorithm 7) -----------------------------------------------------------
+// One block per relevant parent cone (j, gamma) at level d-1, one thread per node x:
+//   F_j(x) = sum over relevant children B_k of B_j of I_P C_{k;alpha}(x) G(x,x_k)/G(x,x_j),
+//   G(x,x_k)/G(x,x_j) = (r_j/r_k) exp(i kappa (r_k - r_j)),  r_k - r_j = (|o|^2 - 2 q.o)/(r_k + r_j),
+// q the node offset from x_j and o the child-centre offset; then the parent interpolant.
+template <int PS, int PT, int PP>
+__global__ void k_prop_f32(const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
+                           const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
+                           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
+                           const float2* __restrict__ cchild, float2* __restrict__ cparent, int sh, float ku,
+                           const float* __restrict__ W, int cstride, int nrhs, int* __restrict__ status) {
+    constexpr int P = PS * PT * PP;
+    __shared__ float2 f[P], tmp[P];
+    const int pc = blockIdx.x;
+    const int r = blockIdx.y;
+    const int n = threadIdx.x;
+    if (n < P) {
+        const int jb = pcone_box[pc];
+        const float3 q = node_grid(gp, PS, PT, PP, pcone_gam[pc], n);
+        const float rj = sqrtf(fmaf(q.x, q.x, fmaf(q.y, q.y, q.z * q.z)));
+        const int4 kj = kp[jb];
+        const float oo = 3.0f * (float)(1 << sh) * (float)(1 << sh);
+        float2 acc = make_float2(0.f, 0.f);
+        const int k1 = pcstart[jb + 1];
+        for (int kb = pcstart[jb]; kb < k1; ++kb) {
+            const int4 kk = kd[kb];
+            const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
+            const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
+            const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
+            const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
+            const int s = __ldg(&slot[(int64_t)kb * g.C + cl.gamma]);
+            if (s < 0) {
+                set_status(status, IFGF_ERR_INTERNAL);
+                continue;
+            }
+            const float2 F = interp_f32<PS, PT, PP>(cchild + ((int64_t)s * nrhs + r) * cstride, cl.ts, cl.tt, cl.tp);
+            const float qo = fmaf(q.x, ox, fmaf(q.y, oy, q.z * oz));
+            const float dr = __fdividef(fmaf(-2.f, qo, oo), cl.r + rj);
+            const float2 e = cis_f32(ku * dr);
+            const float w = __fdividef(rj, cl.r);
+            const float2 ratio = make_float2(e.x * w, e.y * w);
+            const float2 t = cmul(F, ratio);
+            acc.x += t.x;
+            acc.y += t.y;
+        }
+        f[n] = acc;
+    }
+    __syncthreads();
+    const float2 c = cheb_coeffs_smem<PS, PT, PP>(f, tmp, W, n);
+    if (n < P) cparent[((int64_t)pc * nrhs + r) * cstride + n] = c;
+}
+
+template <int PS, int PT, int PP>
+__global__ void k_prop_f64(const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
+                           const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
+                           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
+                           const double2* __restrict__ cchild, double2* __restrict__ cparent, int sh, double kappa,
+                           double a0, double a1, double a2, double Hd, const double* __restrict__ W, int cstride,
+                           int nrhs, int* __restrict__ status) {
+    constexpr int P = PS * PT * PP;
+    __shared__ double2 f[P], tmp[P];
+    const int pc = blockIdx.x;
+    const int r = blockIdx.y;
+    const int n = threadIdx.x;
+    if (n < P) {
+        const int jb = pcone_box[pc];
+        const int gam = pcone_gam[pc];
+        const float3 q = node_grid(gp, PS, PT, PP, gam, n);
+        const int4 kj = kp[jb];
+        const double Hp = 2.0 * Hd;
+        const double xj = a0 + (kj.x + 0.5) * Hp, yj = a1 + (kj.y + 0.5) * Hp, zj = a2 + (kj.z + 0.5) * Hp;
+        const int ip = gam % gp.np, it = (gam / gp.np) % gp.nt, is = gam / (gp.np * gp.nt);
+        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+        const double s = gp.snode64[is * PS + ia], th = gp.tnode64[it * PT + ib], ph = gp.pnode64[ip * PP + ic];
+        const double rr = gp.h64 / s;
+        const double yx = xj + rr * sin(th) * cos(ph), yy = yj + rr * sin(th) * sin(ph), yz = zj + rr * cos(th);
+        const double rj = sqrt((yx - xj) * (yx - xj) + (yy - yj) * (yy - yj) + (yz - zj) * (yz - zj));
+        double2 acc = make_double2(0., 0.);
+        for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
+            const int4 kk = kd[kb];
+            const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
+            const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
+            const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
+            const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
+            const int sl = slot[(int64_t)kb * g.C + cl.gamma];
+            if (sl < 0) {
+                set_status(status, IFGF_ERR_INTERNAL);
+                continue;
+            }
+            const double xk = a0 + (kk.x + 0.5) * Hd, yk = a1 + (kk.y + 0.5) * Hd, zk = a2 + (kk.z + 0.5) * Hd;
+            double ts, tt, tp, rk;
+            local_f64(g, cl.gamma, yx - xk, yy - yk, yz - zk, ts, tt, tp, rk);
+            const double2 F = interp_f64<PS, PT, PP>(cchild + ((int64_t)sl * nrhs + r) * cstride, ts, tt, tp);
+            double sn, cs;
+            sincos(kappa * (rk - rj), &sn, &cs);
+            const double w = rj / rk;
+            const double2 t = cmul(F, make_double2(cs * w, sn * w));
+            acc.x += t.x;
+            acc.y += t.y;
+        }
+        f[n] = acc;
+    }
+    __syncthreads();
+    const double2 c = cheb_coeffs_smem<PS, PT, PP>(f, tmp, W, n);
+    if (n < P) cparent[((int64_t)pc * nrhs + r) * cstride + n] = c;
+}
+
+// ---- Interpolation(d) (Algorithm 8) -----------------------------------------------------------
+// One thread per target x: for every B_k in M^d(x) (the cousins of x's level-d box, Eq. (8)),
+// add I_P C_{k;gamma}(x) G(x, x_k).  Mixed variant: |x - x_k| = |c_A - c_k + d_A| with the
+// integer centre offset c_A - c_k = 2^(D-d+1) n, so
+//   kappa |x - x_k| = (kappa H_d sqrt(|n|^2) mod 2 pi) + kappa u (2 c.d_A + |d_A|^2)/(|x - x_k| + |c|).
+template <int PS, int PT, int PP>
+__global__ void k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
+                             const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
+                             const int32_t* __restrict__ cs, const float4* __restrict__ off,
+                             const int32_t* __restrict__ slot, LevelGrid g, const float2* __restrict__ coef,
+                             const float* __restrict__ phtab, float ku, float inv4piu, float2* __restrict__ Is,
+                             int cstride, int nrhs, int* __restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int r = blockIdx.y;
+    const int A = pbox_d[i];
+    const int4 kl = kD[pbox_D[i]];
+    const int4 kA = kd[A];
+    const float4 o = off[i];
+    const float dax = (float)((2 * kl.x + 1) - ((2 * kA.x + 1) << sh)) + o.x;
+    const float day = (float)((2 * kl.y + 1) - ((2 * kA.y + 1) << sh)) + o.y;
+    const float daz = (float)((2 * kl.z + 1) - ((2 * kA.z + 1) << sh)) + o.z;
+    const float dd = fmaf(dax, dax, fmaf(day, day, daz * daz));
+    const float cscale = (float)(2 << sh);
+    float2 acc = make_float2(0.f, 0.f);
+    const int nc = ncs[A];
+    for (int t = 0; t < nc; ++t) {
+        const int B = cs[(int64_t)A * kMaxCous + t];
+        const int4 kb = kd[B];
+        const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
+        const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
+        const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
+        const ConeLocal cl = locate_f32(g, vx, vy, vz);
+        const int s = __ldg(&slot[(int64_t)B * g.C + cl.gamma]);
+        if (s < 0) {
+            set_status(status, IFGF_ERR_INTERNAL);
+            continue;
+        }
+        const float2 F = interp_f32<PS, PT, PP>(coef + ((int64_t)s * nrhs + r) * cstride, cl.ts, cl.tt, cl.tp);
+        const int nx = kA.x - kb.x, ny = kA.y - kb.y, nz = kA.z - kb.z;
+        const int nn = nx * nx + ny * ny + nz * nz;
+        const float cx = cscale * nx, cy = cscale * ny, cz = cscale * nz;
+        const float cn = cscale * sqrtf((float)nn);
+        const float num = fmaf(2.f, fmaf(cx, dax, fmaf(cy, day, cz * daz)), dd);
+        const float corr = __fdividef(num, cl.r + cn);
+        const float2 e = cis_f32(fmaf(ku, corr, __ldg(&phtab[nn])));
+        const float w = __fdividef(inv4piu, cl.r);
+        const float2 tv = cmul(F, make_float2(e.x * w, e.y * w));
+        acc.x += tv.x;
+        acc.y += tv.y;
+    }
+    float2* dst = Is + (int64_t)r * N + i;
+    const float2 prev = *dst;
+    *dst = make_float2(prev.x + acc.x, prev.y + acc.y);
+}
+
+template <int PS, int PT, int PP>
+__global__ void k_interp_f64(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
+                             const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
+                             const int32_t* __restrict__ cs, const float4* __restrict__ off,
+                             const double* __restrict__ Xs, const int32_t* __restrict__ slot, LevelGrid g,
+                             const double2* __restrict__ coef, double kappa, double a0, double a1, double a2,
+                             double Hd, double2* __restrict__ Is, int cstride, int nrhs, int* __restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int r = blockIdx.y;
+    const int A = pbox_d[i];
+    const int4 kl = kD[pbox_D[i]];
+    const float4 o = off[i];
+    const double xi = Xs[i], yi = Xs[N + i], zi = Xs[2 * N + i];
+    const double inv4pi = 0.079577471545947667884441881686257181;
+    double2 acc = make_double2(0., 0.);
+    for (int t = 0; t < ncs[A]; ++t) {
+        const int B = cs[(int64_t)A * kMaxCous + t];
+        const int4 kb = kd[B];
+        const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
+        const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
+        const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
+        const ConeLocal cl = locate_f32(g, vx, vy, vz);
+        const int s = slot[(int64_t)B * g.C + cl.gamma];
+        if (s < 0) {
+            set_status(status, IFGF_ERR_INTERNAL);
+            continue;
+        }
+        const double xb = a0 + (kb.x + 0.5) * Hd, yb = a1 + (kb.y + 0.5) * Hd, zb = a2 + (kb.z + 0.5) * Hd;
+        double ts, tt, tp, rr;
+        local_f64(g, cl.gamma, xi - xb, yi - yb, zi - zb, ts, tt, tp, rr);
+        const double2 F = interp_f64<PS, PT, PP>(coef + ((int64_t)s * nrhs + r) * cstride, ts, tt, tp);
+        double sn, c;
+        sincos(kappa * rr, &sn, &c);
+        const double w = inv4pi / rr;
+        const double2 tv = cmul(F, make_double2(c * w, sn * w));
+        acc.x += tv.x;
+        acc.y += tv.y;
+    }
+    double2* dst = Is + (int64_t)r * N + i;
+    const double2 prev = *dst;
+    *dst = make_double2(prev.x + acc.x, prev.y + acc.y);
+}
+
+// ---- driver -------------------------------------------------------------------------------
+template <int PS, int PT, int PP>
+void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
+    constexpr int P = PS * PT * PP;
+    constexpr int BT = ((P + 31) / 32) * 32;
+    const int64_t N = p.N;
+    const int D = p.D;
+    const dim3 gN(grid_for(N, kThreads), nrhs);
+    const bool mixed = p.precision == IFGF_PREC_MIXED;
+    const double u = p.u;
+    const double HD = std::ldexp(p.H1, 1 - D);
+    Level& LD = p.L[D];
+    int cur = 0;
+    if (mixed) {
+        const float ku = (float)(p.kappa * u);
+        const float inv4piu = (float)(1.0 / (4.0 * M_PI * u));
+        float2* as = (float2*)p.a_s;
+        float2* Is = (float2*)p.I_s;
+        {
+            TimedScope ts_(TK_PERM, s);
+            IFGF_LAUNCH(k_perm_in<float2>, gN, kThreads, 0, s, (const float2*)dens, p.perm, N, as);
+        }
+        if (near)
+            {
+                TimedScope ts_(TK_NEAR, s);
+                IFGF_LAUNCH(k_near_f32, gN, kThreads, 0, s, N, LD.pbox, LD.k, LD.start, LD.nnb, LD.nb, p.off, as, Is, ku,
+                            inv4piu);
+            }
+        else
+            IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * nrhs, s));
+        const float kh = (float)(p.kappa * LD.g.h64);
+        if (LD.nc > 0)
+            {
+                TimedScope ts_(TK_LEAF, s);
+                IFGF_LAUNCH((k_leaf_f32<PS, PT, PP>), dim3((unsigned)LD.nc, nrhs), BT, 0, s, LD.cone_box, LD.cone_gam,
+                            LD.g, LD.start, p.off, as, N, kh, 1.0f / LD.g.hg, p.Wf, (float2*)p.coef[cur], p.cstride,
+                            nrhs);
+            }
+        for (int d = D; d >= 3; --d) {
+            Level& L = p.L[d];
+            const int sh = D - d;
+            if ((mask >> d) & 1)
+                {
+                    TimedScope ts_(TK_INTERP, s);
+                    IFGF_LAUNCH((k_interp_f32<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs,
+                                L.cs, p.off, L.slot, L.g, (const float2*)p.coef[cur], L.phtab, ku, inv4piu, Is, p.cstride,
+                                nrhs, p.d_status);
+                }
+            if (d == 3) break;
+            Level& Lp = p.L[d - 1];
+            if (Lp.nc > 0)
+                {
+                    TimedScope ts_(TK_PROP, s);
+                    IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)Lp.nc, nrhs), BT, 0, s, Lp.cone_box, Lp.cone_gam,
+                                Lp.k, Lp.cstart, Lp.g, L.k, L.slot, L.g, (const float2*)p.coef[cur],
+                                (float2*)p.coef[1 - cur], sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
+                }
+            cur = 1 - cur;
+        }
+        {
+            TimedScope ts_(TK_PERM, s);
+            IFGF_LAUNCH(k_perm_out<float2>, gN, kThreads, 0, s, Is, p.perm, N, (float2*)out);
+        }
+    } else {
+        double2* as = (double2*)p.a_s;
+        double2* Is = (double2*)p.I_s;
+        {
+            TimedScope ts_(TK_PERM, s);
+            IFGF_LAUNCH(k_perm_in<double2>, gN, kThreads, 0, s, (const double2*)dens, p.perm, N, as);
+        }
+        if (near)
+            {
+                TimedScope ts_(TK_NEAR, s);
+                IFGF_LAUNCH(k_near_f64, gN, kThreads, 0, s, N, LD.pbox, LD.start, LD.nnb, LD.nb, p.Xs, as, Is, p.kappa);
+            }
+        else
+            IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(double2) * N * nrhs, s));
+        if (LD.nc > 0)
+            {
+                TimedScope ts_(TK_LEAF, s);
+                IFGF_LAUNCH((k_leaf_f64<PS, PT, PP>), dim3((unsigned)LD.nc, nrhs), BT, 0, s, LD.cone_box, LD.cone_gam,
+                            LD.g, LD.start, LD.k, p.Xs, as, N, p.kappa, p.a[0], p.a[1], p.a[2], HD, p.Wd,
+                            (double2*)p.coef[cur], p.cstride, nrhs);
+            }
+        for (int d = D; d >= 3; --d) {
+            Level& L = p.L[d];
+            const int sh = D - d;
+            const double Hd = std::ldexp(p.H1, 1 - d);
+            if ((mask >> d) & 1)
+                {
+                    TimedScope ts_(TK_INTERP, s);
+                    IFGF_LAUNCH((k_interp_f64<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs,
+                                L.cs, p.off, p.Xs, L.slot, L.g, (const double2*)p.coef[cur], p.kappa, p.a[0], p.a[1],
+                                p.a[2], Hd, Is, p.cstride, nrhs, p.d_status);
+                }
+            if (d == 3) break;
+            Level& Lp = p.L[d - 1];
+            if (Lp.nc > 0)
+                {
+                    TimedScope ts_(TK_PROP, s);
+                    IFGF_LAUNCH((k_prop_f64<PS, PT, PP>), dim3((unsigned)Lp.nc, nrhs), BT, 0, s, Lp.cone_box, Lp.cone_gam,
+                                Lp.k, Lp.cstart, Lp.g, L.k, L.slot, L.g, (const double2*)p.coef[cur],
+                                (double2*)p.coef[1 - cur], sh, p.kappa, p.a[0], p.a[1], p.a[2], Hd, p.Wd, p.cstride, nrhs,
+                                p.d_status);
+                }
+            cur = 1 - cur;
+        }
+        {
+            TimedScope ts_(TK_PERM, s);
+            IFGF_LAUNCH(k_perm_out<double2>, gN, kThreads, 0, s, Is, p.perm, N, (double2*)out);
+        }
+    }
+}
+
+}  // namespace
+
+void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
+    if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
+        run_apply<3, 5, 5>(p, dens, nrhs, out, s, near, mask);
+    else if (p.Ps == 5 && p.Pt == 7 && p.Pp == 7)
+        run_apply<5, 7, 7>(p, dens, nrhs, out, s, near, mask);
+    else
+        fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
+}
+
+}  // namespace ifgf

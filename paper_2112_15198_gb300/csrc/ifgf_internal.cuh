@@ -1,0 +1,405 @@
+// Internal data structures and device helpers of the GB300 IFGF library.
+//
+// Geometry conventions (shared by the plan builder and the apply kernels):
+//  - Root cube B^1 (Sec. 2): a = centre(bbox) - H1/2, H1 = largest extent * (1 + 2^-20).
+//  - Level-d boxes have side H_d = H1 / 2^(d-1); the grid unit is u = H_D / 2, so every box
+//    centre lies at a + u * (odd integer vector) and offsets between centres are exact small
+//    integers in grid units.
+//  - Each sorted point keeps its FP32 offset from its leaf centre in grid units, so the
+//    offset of a point from any box centre is (exact integer) + (FP32 leaf offset).
+//  - Cone segments of level d: uniform grids over s = h_d / r in [0, eta], theta in [0, pi],
+//    phi in [0, 2 pi), h_d = sqrt(3)/2 H_d, eta = sqrt(3)/3 (Sec. 2, box-centred cones).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ifgf.h"
+
+namespace ifgf {
+
+constexpr int kKeyLevel = 21;  // finest level of the sort key: 20 bits per axis
+constexpr int kMaxLevel = 21;
+constexpr int kMaxNbr = 27;    // |N B| <= 27
+constexpr int kMaxCous = 189;  // |M B| <= 189 (Sec. 3.3)
+constexpr int kMaxOrder = 8;
+
+extern std::atomic<int64_t> g_launches;
+
+// Per-level cone grid: counts, exact-classification tables and interpolation-node tables.
+struct LevelGrid {
+    int ns, nt, np, C;         // cone counts per direction, C = ns*nt*np
+    float hg;                  // circumradius h_d in grid units
+    float s_scale, t_scale, p_scale;  // ns/eta, nt/pi, np/(2 pi): candidate bins
+    float s2w, t2w, p2w;       // 2/ds, 2/dt, 2/dp: local coordinate scales
+    double ds64, dt64, dp64;   // interval widths
+    double h64;                // circumradius in physical units
+    const float* R2;           // [ns]  (h/(i ds))^2, grid units
+    const float* C2;           // [nt]  cos^2(i pi/nt)
+    const int* cpos;           // [nt]  cos(i pi/nt) >= 0
+    const float* cph;          // [np]  cos(2 pi j/np)
+    const float* sph;          // [np]  sin(2 pi j/np)
+    const float* rho;          // [ns*Ps] node radius h/s in grid units
+    const float* ctn;          // [nt*Pt] cos of theta nodes
+    const float* stn;          // [nt*Pt] sin of theta nodes
+    const float* cpn;          // [np*Pp] cos of phi nodes
+    const float* spn;          // [np*Pp] sin of phi nodes
+    const float* snode;        // [ns*Ps] s of nodes (FP32)
+    const double* snode64;     // [ns*Ps] s of nodes
+    const double* tnode64;     // [nt*Pt] theta of nodes
+    const double* pnode64;     // [np*Pp] phi of nodes
+};
+
+struct Level {
+    int32_t n = 0;                 // relevant boxes R_B^d
+    uint64_t* key = nullptr;       // [n] Morton keys, ascending
+    int32_t* start = nullptr;      // [n+1] sorted point ranges
+    int32_t* parent = nullptr;     // [n] box index at level d-1
+    int32_t* cstart = nullptr;     // [n+1] first child at level d+1
+    int4* k = nullptr;             // [n] integer box coordinates
+    int32_t* pbox = nullptr;       // [N] box of every sorted point
+    int32_t* nnb = nullptr;        // [n]
+    int32_t* nb = nullptr;         // [n*27] ascending
+    int32_t* ncs = nullptr;        // [n]
+    int32_t* cs = nullptr;         // [n*189] ascending
+    LevelGrid g{};
+    int64_t nc = 0;                // relevant cones R_C^d
+    int32_t* slot = nullptr;       // [n*C] cone index or -1
+    int32_t* cone_box = nullptr;   // [nc]
+    int32_t* cone_gam = nullptr;   // [nc]
+    float* phtab = nullptr;        // [28] (kappa H_d sqrt(m)) mod 2 pi, m = |k_A - k_B|^2
+    std::vector<int32_t> host_grid;  // (ns, nt, np)
+};
+
+struct Plan {
+    int64_t N = 0;
+    int D = 0;
+    double kappa = 0;
+    int Ps = 3, Pt = 5, Pp = 5, P = 75;
+    int cstride = 76;              // complex entries per cone and density vector
+    int precision = IFGF_PREC_MIXED;
+    int max_nrhs = 1;
+    double a[3] = {0, 0, 0};
+    double H1 = 0, u = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int32_t* perm = nullptr;       // [N] sorted -> caller index
+    uint64_t* key = nullptr;       // [N] sorted keys
+    double* Xs = nullptr;          // [3][N] sorted coordinates
+    float4* off = nullptr;         // [N] leaf offsets (grid units), w unused
+    Level L[kMaxLevel + 1];
+    float* Wf = nullptr;           // analysis matrices Ws | Wt | Wp (FP32)
+    double* Wd = nullptr;          // same in FP64
+    void* a_s = nullptr;           // sorted densities [nrhs][N]
+    void* I_s = nullptr;           // sorted output [nrhs][N]
+    void* coef[2] = {nullptr, nullptr};
+    int64_t coef_cap = 0;          // cones per coefficient buffer
+    int* d_status = nullptr;       // sticky device status
+    std::vector<void*> allocs;
+};
+
+// ---- errors -------------------------------------------------------------------------
+struct Error {
+    ifgf_status status;
+    std::string what;
+};
+void set_last_error(const std::string& s);
+[[noreturn]] void fail(ifgf_status s, const std::string& what);
+void cuda_check(cudaError_t e, const char* what);
+#define IFGF_CUDA(expr) ::ifgf::cuda_check((expr), #expr)
+
+template <class T>
+T* dalloc(Plan& p, size_t count) {
+    void* ptr = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&ptr, bytes, p.stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(IFGF_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    p.allocs.push_back(ptr);
+    return static_cast<T*>(ptr);
+}
+
+// Stream-ordered release of every allocation made after `mark` (temporaries of one stage).
+inline void dfree_from(Plan& p, size_t mark) {
+    while (p.allocs.size() > mark) {
+        cudaFreeAsync(p.allocs.back(), p.stream);
+        p.allocs.pop_back();
+    }
+}
+
+// Stream-ordered release of one allocation.
+inline void dfree_ptr(Plan& p, void* ptr) {
+    for (size_t i = p.allocs.size(); i-- > 0;)
+        if (p.allocs[i] == ptr) {
+            cudaFreeAsync(ptr, p.stream);
+            p.allocs.erase(p.allocs.begin() + (std::ptrdiff_t)i);
+            return;
+        }
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+#define IFGF_LAUNCH(kernel, grid, block, smem, stream, ...)                     \
+    do {                                                                       \
+        kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
+        ::ifgf::g_launches.fetch_add(1, std::memory_order_relaxed);            \
+        ::ifgf::cuda_check(cudaGetLastError(), #kernel);                       \
+    } while (0)
+
+// ---- live kernel timing (opt-in; CUDA events around each hot kernel) -------------------
+enum TimingKind { TK_PERM = 0, TK_NEAR = 1, TK_LEAF = 2, TK_PROP = 3, TK_INTERP = 4, TK_PLAN = 5, TK_COUNT = 6 };
+struct TimedScope {
+    TimedScope(int kind, cudaStream_t s);
+    ~TimedScope();
+    int kind;
+    cudaStream_t stream;
+    cudaEvent_t start = nullptr;
+};
+
+// ---- scan / sort utilities (util.cu) --------------------------------------------------
+// Exclusive prefix sum of n int32 values into out (may alias in); returns nothing; the
+// total is out[n-1] + in[n-1] (callers read it back when needed).
+void exclusive_scan_i32(Plan& p, const int32_t* in, int32_t* out, int64_t n);
+// Stable LSD radix sort of (key, val) pairs over key bits [0, end_bit); result in keys/vals.
+void radix_sort_pairs(Plan& p, uint64_t* keys, int32_t* vals, int64_t n, int end_bit);
+
+// ---- stages -----------------------------------------------------------------------------
+void build_plan(Plan& p, const double* points, const ifgf_options& opt, int levels);
+void destroy_plan(Plan& p);
+void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask);
+
+// =========================================================================================
+// Device helpers
+// =========================================================================================
+
+// r^2 = (vx*vx + vy*vy) + vz*vz, each operation correctly rounded (no contraction).
+__device__ __forceinline__ float rn_r2(float vx, float vy, float vz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
+}
+
+// Exact cone classification of an FP32 grid-unit offset v (r2 = rn_r2(v)).  Each bin index
+// is the number of edges the point lies on or beyond, decided by correctly rounded FP32
+// products/sums and comparisons; (cs, ct, cp) are candidate bins from approximate spherical
+// coordinates, from which the exact count is reached by stepping across edges (the edge
+// predicates are monotone in the edge index).
+//   s:     edge i (1 <= i < ns) passed iff r2 <= R2[i]                 (s >= i ds)
+//   theta: edge i (1 <= i < nt) passed iff vz <= cos(theta_i) r, in squared form
+//   phi:   edge j (1 <= j < np) passed iff phi >= phi_j, from the half plane left of edge j
+//          and the lower half plane H; 0 on the z axis.
+__device__ __forceinline__ int classify_exact(const LevelGrid& g, float vx, float vy, float vz, float r2, int cs,
+                                              int ct, int cp) {
+    int is = min(max(cs, 0), g.ns - 1);
+    while (is > 0 && !(r2 <= __ldg(&g.R2[is]))) --is;
+    while (is + 1 < g.ns && (r2 <= __ldg(&g.R2[is + 1]))) ++is;
+
+    const float z2 = __fmul_rn(vz, vz);
+    const bool zneg = vz < 0.0f;
+    int it = min(max(ct, 0), g.nt - 1);
+    auto Q = [&](int i) -> bool {
+        float c2r = __fmul_rn(__ldg(&g.C2[i]), r2);
+        return __ldg(&g.cpos[i]) ? (zneg || z2 <= c2r) : (zneg && z2 >= c2r);
+    };
+    while (it > 0 && !Q(it)) --it;
+    while (it + 1 < g.nt && Q(it + 1)) ++it;
+
+    int ip = 0;
+    if (!(vx == 0.0f && vy == 0.0f)) {
+        const bool H = (vy < 0.0f) || (vy == 0.0f && vx < 0.0f);
+        auto GE = [&](int j) -> bool {
+            bool Lj = __fsub_rn(__fmul_rn(__ldg(&g.cph[j]), vy), __fmul_rn(__ldg(&g.sph[j]), vx)) >= 0.0f;
+            int j2 = 2 * j;
+            return j2 < g.np ? (Lj || H) : (j2 == g.np ? H : (Lj && H));
+        };
+        ip = min(max(cp, 0), g.np - 1);
+        while (ip > 0 && !GE(ip)) --ip;
+        while (ip + 1 < g.np && GE(ip + 1)) ++ip;
+    }
+    return (is * g.nt + it) * g.np + ip;
+}
+
+// Approximate spherical coordinates (FP32) of a grid-unit offset and the exact cone; returns
+// gamma and the local coordinates (t_s, t_theta, t_phi) in [-1, 1] (slightly beyond at edges).
+struct ConeLocal {
+    int gamma;
+    float ts, tt, tp;
+    float r;  // |v| (approximate)
+};
+
+__device__ __forceinline__ ConeLocal locate_f32(const LevelGrid& g, float vx, float vy, float vz) {
+    const float r2 = rn_r2(vx, vy, vz);
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float s = g.hg * rinv;
+    const float rxy = sqrtf(fmaf(vx, vx, vy * vy));
+    const float th = atan2f(rxy, vz);
+    float ph = atan2f(vy, vx);
+    if (ph < 0.0f) ph += 6.28318530717958647692f;
+    const int cs = (int)(s * g.s_scale);
+    const int ct = (int)(th * g.t_scale);
+    const int cp = (int)(ph * g.p_scale);
+    const int gam = classify_exact(g, vx, vy, vz, r2, cs, ct, cp);
+    const int ip = gam % g.np;
+    const int it = (gam / g.np) % g.nt;
+    const int is = gam / (g.np * g.nt);
+    ConeLocal o;
+    o.gamma = gam;
+    o.r = r;
+    o.ts = fmaf(s, g.s2w, -(float)(2 * is + 1));
+    o.tt = fmaf(th, g.t2w, -(float)(2 * it + 1));
+    float tp = fmaf(ph, g.p2w, -(float)(2 * ip + 1));
+    const float span = (float)(2 * g.np);  // 2 pi in local units
+    if (tp > (float)g.np) tp -= span;
+    if (tp < -(float)g.np) tp += span;
+    o.tp = tp;
+    return o;
+}
+
+// FP64 local coordinates of a physical offset v inside cone gamma of a level grid.
+__device__ __forceinline__ void local_f64(const LevelGrid& g, int gam, double vx, double vy, double vz, double& ts,
+                                          double& tt, double& tp, double& r) {
+    const int ip = gam % g.np;
+    const int it = (gam / g.np) % g.nt;
+    const int is = gam / (g.np * g.nt);
+    const double rxy = sqrt(vx * vx + vy * vy);
+    r = sqrt(vx * vx + vy * vy + vz * vz);
+    const double s = g.h64 / r;
+    const double th = atan2(rxy, vz);
+    const double ph = atan2(vy, vx);
+    ts = (s - g.ds64 * (is + 0.5)) / (0.5 * g.ds64);
+    tt = (th - g.dt64 * (it + 0.5)) / (0.5 * g.dt64);
+    double dph = ph - g.dp64 * (ip + 0.5);
+    const double twopi = 6.283185307179586476925286766559;
+    if (dph > 3.14159265358979323846) dph -= twopi;
+    if (dph > 3.14159265358979323846) dph -= twopi;
+    if (dph <= -3.14159265358979323846) dph += twopi;
+    if (dph <= -3.14159265358979323846) dph += twopi;
+    tp = dph / (0.5 * g.dp64);
+}
+
+// Chebyshev polynomials T_0..T_{P-1}(t) by the three-term recurrence.
+template <int P, class T>
+__device__ __forceinline__ void cheb_T(T t, T* v) {
+    v[0] = T(1);
+    if (P > 1) v[1] = t;
+    const T t2 = t + t;
+#pragma unroll
+    for (int n = 2; n < P; ++n) v[n] = t2 * v[n - 1] - v[n - 2];
+}
+
+// Interpolant sum_abc c_abc T_a(ts) T_b(tt) T_c(tp), contracted phi, then theta, then s,
+// with packed FP32x2 FMAs (re and im share the real basis weight).
+template <int PS, int PT, int PP>
+__device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float ts, float tt, float tp) {
+    float Ts[PS], Tt[PT], Tp[PP];
+    cheb_T<PS>(ts, Ts);
+    cheb_T<PT>(tt, Tt);
+    cheb_T<PP>(tp, Tp);
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < PS; ++a) {
+        float2 aa = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < PT; ++b) {
+            float2 bb = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                const float2 co = __ldg(c + (a * PT + b) * PP + q);
+                bb = __ffma2_rn(co, make_float2(Tp[q], Tp[q]), bb);
+            }
+            aa = __ffma2_rn(bb, make_float2(Tt[b], Tt[b]), aa);
+        }
+        acc = __ffma2_rn(aa, make_float2(Ts[a], Ts[a]), acc);
+    }
+    return acc;
+}
+
+template <int PS, int PT, int PP>
+__device__ __forceinline__ double2 interp_f64(const double2* __restrict__ c, double ts, double tt, double tp) {
+    double Ts[PS], Tt[PT], Tp[PP];
+    cheb_T<PS>(ts, Ts);
+    cheb_T<PT>(tt, Tt);
+    cheb_T<PP>(tp, Tp);
+    double2 acc = make_double2(0., 0.);
+#pragma unroll
+    for (int a = 0; a < PS; ++a) {
+        double2 aa = make_double2(0., 0.);
+#pragma unroll
+        for (int b = 0; b < PT; ++b) {
+            double2 bb = make_double2(0., 0.);
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                const double2 co = c[(a * PT + b) * PP + q];
+                bb.x = fma(co.x, Tp[q], bb.x);
+                bb.y = fma(co.y, Tp[q], bb.y);
+            }
+            aa.x = fma(bb.x, Tt[b], aa.x);
+            aa.y = fma(bb.y, Tt[b], aa.y);
+        }
+        acc.x = fma(aa.x, Ts[a], acc.x);
+        acc.y = fma(aa.y, Ts[a], acc.y);
+    }
+    return acc;
+}
+
+// Reduction of an angle to [-pi, pi] (Cody and Waite's method: 2 pi = c1 + c2 + c3 with c1
+// short enough that k*c1 is exact; each step is one fused multiply-add).
+__device__ __forceinline__ float reduce_2pi(float x) {
+    const float k = rintf(x * 0.159154943091895335768883763f);
+    float r = fmaf(-k, 6.28125f, x);
+    r = fmaf(-k, 0.0019353071693331003f, r);
+    r = fmaf(-k, 1.0253131677018246e-11f, r);
+    return r;
+}
+
+// exp(i x) for an FP32 phase, after reduction.
+__device__ __forceinline__ float2 cis_f32(float x) {
+    float s, c;
+    __sincosf(reduce_2pi(x), &s, &c);
+    return make_float2(c, s);
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// Morton interleave of three 21-bit coordinates (bit 3b = x_b, 3b+1 = y_b, 3b+2 = z_b).
+__host__ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+__host__ __device__ __forceinline__ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+}  // namespace ifgf

@@ -1,0 +1,571 @@
+// Plan construction on the GPU: the octree of Sec. 2 with the Morton order of Sec. 3.2.1,
+// neighbour and cousin sets of Eq. (2), and the relevant cone segments of Eq. (4).
+//
+// All heavy steps run as device kernels; the host only reads back sizes (bounding box,
+// boxes per level, cones per level) to size the next allocations.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ifgf_internal.cuh"
+
+namespace ifgf {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---- bounding box -----------------------------------------------------------------------
+__global__ void k_bbox_partial(const double* __restrict__ X, int64_t N, double* __restrict__ part) {
+    __shared__ double smin[3][kThreads], smax[3][kThreads];
+    __shared__ int sbad[kThreads];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v = X[(int64_t)c * N + i];
+            if (!isfinite(v)) bad = 1;
+            mn[c] = fmin(mn[c], v);
+            mx[c] = fmax(mx[c], v);
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        smin[c][threadIdx.x] = mn[c];
+        smax[c][threadIdx.x] = mx[c];
+    }
+    sbad[threadIdx.x] = bad;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            for (int c = 0; c < 3; ++c) {
+                smin[c][threadIdx.x] = fmin(smin[c][threadIdx.x], smin[c][threadIdx.x + o]);
+                smax[c][threadIdx.x] = fmax(smax[c][threadIdx.x], smax[c][threadIdx.x + o]);
+            }
+            sbad[threadIdx.x] |= sbad[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 3; ++c) {
+            part[blockIdx.x * 7 + c] = smin[c][0];
+            part[blockIdx.x * 7 + 3 + c] = smax[c][0];
+        }
+        part[blockIdx.x * 7 + 6] = sbad[0];
+    }
+}
+
+// ---- keys -------------------------------------------------------------------------------
+// Level-21 box index k = floor(u 2^20) (clamped), u = (x - a)/H1, then the Morton key.
+__global__ void k_keys(const double* __restrict__ X, int64_t N, double a0, double a1, double a2, double H1,
+                       uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double a[3] = {a0, a1, a2};
+    uint32_t k[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double u = __ddiv_rn(__dsub_rn(X[(int64_t)c * N + i], a[c]), H1);
+        double f = floor(__dmul_rn(u, 1048576.0));
+        f = fmin(fmax(f, 0.0), 1048575.0);
+        k[c] = (uint32_t)f;
+    }
+    keys[i] = morton3(k[0], k[1], k[2]);
+    vals[i] = (int32_t)i;
+}
+
+__global__ void k_gather_points(const double* __restrict__ X, int64_t N, const int32_t* __restrict__ perm,
+                                double* __restrict__ Xs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int64_t o = perm[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Xs[(int64_t)c * N + i] = X[(int64_t)c * N + o];
+}
+
+// Coarsest level at which the keys of points i-1 and i differ: boxes split there and below.
+__global__ void k_level_split(const uint64_t* __restrict__ keys, int64_t N, uint8_t* __restrict__ d0,
+                              unsigned long long* __restrict__ hist) {
+    __shared__ unsigned int h[24];
+    if (threadIdx.x < 24) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        int lev = 0;
+        if (i > 0) {
+            const uint64_t x = keys[i] ^ keys[i - 1];
+            if (x == 0)
+                lev = 22;
+            else
+                lev = kKeyLevel - (63 - __clzll((long long)x)) / 3;
+            atomicAdd(&h[lev], 1u);
+        }
+        d0[i] = (uint8_t)lev;
+    }
+    __syncthreads();
+    if (threadIdx.x < 24 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+__global__ void k_level_flags(const uint8_t* __restrict__ d0, int64_t N, int d, int32_t* __restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    flag[i] = (i == 0 || (int)d0[i] <= d) ? 1 : 0;
+}
+
+__global__ void k_level_boxes(const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                              const uint64_t* __restrict__ keys, int64_t N, int d, int32_t nbox,
+                              int32_t* __restrict__ start, uint64_t* __restrict__ bkey, int4* __restrict__ bk,
+                              int32_t* __restrict__ pbox) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) start[nbox] = (int32_t)N;
+    if (i >= N) return;
+    const int32_t f = flag[i], b = pos[i] + f - 1;
+    pbox[i] = b;
+    if (f) {
+        const uint64_t key = keys[i] >> (3 * (kKeyLevel - d));
+        start[b] = (int32_t)i;
+        bkey[b] = key;
+        bk[b] = make_int4((int)compact3(key), (int)compact3(key >> 1), (int)compact3(key >> 2), 0);
+    }
+}
+
+__global__ void k_parents(const int32_t* __restrict__ start, int32_t n, const int32_t* __restrict__ pbox_up,
+                          int32_t* __restrict__ parent) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    parent[b] = pbox_up ? pbox_up[start[b]] : -1;
+}
+
+__global__ void k_child_start(const int32_t* __restrict__ parent_child, int32_t nchild, int32_t nparent,
+                              int32_t* __restrict__ cstart) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) cstart[nparent] = nchild;
+    if (c >= nchild) return;
+    const int p = parent_child[c];
+    if (c == 0 || parent_child[c - 1] != p) cstart[p] = c;
+}
+
+// Offset of every sorted point from its leaf centre in grid units u = H_D/2, rounded to FP32.
+__global__ void k_offsets(const double* __restrict__ Xs, int64_t N, double a0, double a1, double a2, double H1,
+                          double scale, const int32_t* __restrict__ pboxD, const int4* __restrict__ kD,
+                          float4* __restrict__ off) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int4 k = kD[pboxD[i]];
+    const double a[3] = {a0, a1, a2};
+    const int kk[3] = {k.x, k.y, k.z};
+    float o[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double u = __ddiv_rn(__dsub_rn(Xs[(int64_t)c * N + i], a[c]), H1);
+        const double t = __dmul_rn(u, scale);
+        o[c] = __double2float_rn(__dsub_rn(t, (double)(2 * (int64_t)kk[c] + 1)));
+    }
+    off[i] = make_float4(o[0], o[1], o[2], 0.f);
+}
+
+__device__ __forceinline__ int find_box(const uint64_t* __restrict__ keys, int n, uint64_t key) {
+    int lo = 0, hi = n - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const uint64_t k = keys[mid];
+        if (k == key) return mid;
+        if (k < key)
+            lo = mid + 1;
+        else
+            hi = mid - 1;
+    }
+    return -1;
+}
+
+// Neighbours N B (Eq. (2)): relevant boxes with ||j - k||_inf <= 1, ascending.
+__global__ void k_neighbours(const uint64_t* __restrict__ keys, const int4* __restrict__ bk, int n, int d,
+                             int32_t* __restrict__ nnb, int32_t* __restrict__ nb) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int4 k = bk[b];
+    const int side = 1 << (d - 1);
+    int list[kMaxNbr];
+    int cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = k.x + dx, y = k.y + dy, z = k.z + dz;
+                if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
+                const int q = find_box(keys, n, morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+                if (q >= 0) {
+                    int j = cnt++;
+                    while (j > 0 && list[j - 1] > q) {
+                        list[j] = list[j - 1];
+                        --j;
+                    }
+                    list[j] = q;
+                }
+            }
+    nnb[b] = cnt;
+    for (int t = 0; t < cnt; ++t) nb[(int64_t)b * kMaxNbr + t] = list[t];
+}
+
+// Cousins M B (Eq. (2)): children of the parent's neighbours that are not neighbours.  The
+// parent's neighbours are ascending and children are contiguous, so the list is ascending.
+__global__ void k_cousins(const int4* __restrict__ bk, const int32_t* __restrict__ parent, int n,
+                          const int32_t* __restrict__ pnnb, const int32_t* __restrict__ pnb,
+                          const int32_t* __restrict__ pcstart, int32_t* __restrict__ ncs, int32_t* __restrict__ cs) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int4 k = bk[b];
+    const int pb = parent[b];
+    int cnt = 0;
+    for (int t = 0; t < pnnb[pb]; ++t) {
+        const int q = pnb[(int64_t)pb * kMaxNbr + t];
+        for (int c = pcstart[q]; c < pcstart[q + 1]; ++c) {
+            const int4 kc = bk[c];
+            const int m = max(abs(kc.x - k.x), max(abs(kc.y - k.y), abs(kc.z - k.z)));
+            if (m > 1 && cnt < kMaxCous) cs[(int64_t)b * kMaxCous + cnt++] = c;
+        }
+    }
+    ncs[b] = cnt;
+}
+
+// ---- cone activation (Eq. (4), discrete form) -------------------------------------------
+// Cousin points x in V B: every point marks, in each cousin box of its level-d box, the cone
+// that contains it.
+__global__ void k_mark_cousin_points(int64_t N, int D, int d, const int32_t* __restrict__ pbox_d,
+                                     const int32_t* __restrict__ pbox_D, const int4* __restrict__ kD,
+                                     const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
+                                     const int32_t* __restrict__ cs, const float4* __restrict__ off, LevelGrid g,
+                                     int32_t* __restrict__ mark) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int A = pbox_d[i];
+    const int4 kl = kD[pbox_D[i]];
+    const float4 o = off[i];
+    const int sh = D - d;
+    const int nc = ncs[A];
+    for (int t = 0; t < nc; ++t) {
+        const int B = cs[(int64_t)A * kMaxCous + t];
+        const int4 kb = kd[B];
+        const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
+        const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
+        const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
+        const ConeLocal cl = locate_f32(g, vx, vy, vz);
+        mark[(int64_t)B * g.C + cl.gamma] = 1;
+    }
+}
+
+// Node offset (grid units) of node n of cone gamma, from the parent's node tables.
+__device__ __forceinline__ float3 node_grid(const LevelGrid& gp, int Ps, int Pt, int Pp, int gam, int n) {
+    const int ip = gam % gp.np, it = (gam / gp.np) % gp.nt, is = gam / (gp.np * gp.nt);
+    const int c = n % Pp, b = (n / Pp) % Pt, a = n / (Pp * Pt);
+    const float rho = gp.rho[is * Ps + a];
+    const float st = gp.stn[it * Pt + b], ct = gp.ctn[it * Pt + b];
+    const float cp = gp.cpn[ip * Pp + c], sp = gp.spn[ip * Pp + c];
+    return make_float3(__fmul_rn(rho, __fmul_rn(st, cp)), __fmul_rn(rho, __fmul_rn(st, sp)), __fmul_rn(rho, ct));
+}
+
+// Nodes of the relevant parent cones: every node of every relevant level-(d-1) cone marks,
+// in each child box of the cone's box, the cone that contains it.
+__global__ void k_mark_parent_nodes(int64_t ncp, int P, int Ps, int Pt, int Pp, int D, int d,
+                                    const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
+                                    const int4* __restrict__ kp, const int32_t* __restrict__ pcstart,
+                                    const int4* __restrict__ kd, LevelGrid gp, LevelGrid g,
+                                    int32_t* __restrict__ mark) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncp * P) return;
+    const int64_t pc = t / P;
+    const int n = (int)(t - pc * P);
+    const int jb = pcone_box[pc];
+    const float3 q = node_grid(gp, Ps, Pt, Pp, pcone_gam[pc], n);
+    const int4 kj = kp[jb];
+    const int sh = D - d;
+    for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
+        const int4 kk = kd[kb];
+        const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
+        const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
+        const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
+        const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
+        mark[(int64_t)kb * g.C + cl.gamma] = 1;
+    }
+}
+
+__global__ void k_finalize_cones(int32_t* __restrict__ slot, const int32_t* __restrict__ pos, int64_t total, int C,
+                                 int32_t* __restrict__ cone_box, int32_t* __restrict__ cone_gam) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    if (slot[e]) {
+        const int32_t s = pos[e];
+        slot[e] = s;
+        cone_box[s] = (int32_t)(e / C);
+        cone_gam[s] = (int32_t)(e % C);
+    } else {
+        slot[e] = -1;
+    }
+}
+
+// ---- host-side tables (the same formulas as the method's statement; see readings) --------
+double cheb_node(int j, int P) { return std::cos(M_PI * (2.0 * j + 1.0) / (2.0 * P)); }
+double node_in(int idx, double w, double t) { return w * ((double)idx + 0.5 * (1.0 + t)); }
+
+template <class T>
+T* upload(Plan& p, const std::vector<T>& h) {
+    T* d = dalloc<T>(p, h.size());
+    if (!h.empty()) IFGF_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, p.stream));
+    return d;
+}
+
+void build_grid(Plan& p, int d, const ifgf_options& opt, std::vector<std::vector<char>>& keep) {
+    const double eta = std::sqrt(3.0) / 3.0;
+    const double Hd = std::ldexp(p.H1, 1 - d);
+    int e = 0;
+    while (p.kappa > 0.0 && e < 24 && p.kappa * Hd > 2.0 * M_PI * opt.tau * std::ldexp(1.0, e)) ++e;
+    const int ns = opt.base_cones[0] << e, nt = opt.base_cones[1] << e, np = opt.base_cones[2] << e;
+    LevelGrid& g = p.L[d].g;
+    g.ns = ns;
+    g.nt = nt;
+    g.np = np;
+    const int64_t C = (int64_t)ns * nt * np;
+    if (C > (int64_t)1 << 30) fail(IFGF_ERR_UNSUPPORTED, "cone grid too fine for the dense cone table");
+    g.C = (int)C;
+    g.ds64 = eta / ns;
+    g.dt64 = M_PI / nt;
+    g.dp64 = 2.0 * M_PI / np;
+    g.h64 = 0.5 * std::sqrt(3.0) * Hd;
+    const double hgd = std::sqrt(3.0) * std::ldexp(1.0, p.D - d);
+    g.hg = (float)hgd;
+    g.s_scale = (float)(ns / eta);
+    g.t_scale = (float)(nt / M_PI);
+    g.p_scale = (float)(np / (2.0 * M_PI));
+    g.s2w = (float)(2.0 / g.ds64);
+    g.t2w = (float)(2.0 / g.dt64);
+    g.p2w = (float)(2.0 / g.dp64);
+    std::vector<float> R2(ns, INFINITY), C2(nt), cph(np), sph(np);
+    std::vector<int> cpos(nt);
+    for (int i = 1; i < ns; ++i) {
+        const double R = hgd / ((double)i * g.ds64);
+        R2[i] = (float)(R * R);
+    }
+    for (int i = 0; i < nt; ++i) {
+        const double c = std::cos(M_PI * (double)i / (double)nt);
+        C2[i] = (float)(c * c);
+        cpos[i] = c >= 0.0;
+    }
+    for (int j = 0; j < np; ++j) {
+        cph[j] = (float)std::cos(2.0 * M_PI * (double)j / (double)np);
+        sph[j] = (float)std::sin(2.0 * M_PI * (double)j / (double)np);
+    }
+    std::vector<float> rho(ns * p.Ps), sn(ns * p.Ps), ctn(nt * p.Pt), stn(nt * p.Pt), cpn(np * p.Pp), spn(np * p.Pp);
+    std::vector<double> sn64(ns * p.Ps), tn64(nt * p.Pt), pn64(np * p.Pp);
+    for (int is = 0; is < ns; ++is)
+        for (int a = 0; a < p.Ps; ++a) {
+            const double s = node_in(is, g.ds64, cheb_node(a, p.Ps));
+            rho[is * p.Ps + a] = (float)(hgd / s);
+            sn[is * p.Ps + a] = (float)s;
+            sn64[is * p.Ps + a] = s;
+        }
+    for (int it = 0; it < nt; ++it)
+        for (int b = 0; b < p.Pt; ++b) {
+            const double th = node_in(it, g.dt64, cheb_node(b, p.Pt));
+            ctn[it * p.Pt + b] = (float)std::cos(th);
+            stn[it * p.Pt + b] = (float)std::sin(th);
+            tn64[it * p.Pt + b] = th;
+        }
+    for (int ip = 0; ip < np; ++ip)
+        for (int c = 0; c < p.Pp; ++c) {
+            const double ph = node_in(ip, g.dp64, cheb_node(c, p.Pp));
+            cpn[ip * p.Pp + c] = (float)std::cos(ph);
+            spn[ip * p.Pp + c] = (float)std::sin(ph);
+            pn64[ip * p.Pp + c] = ph;
+        }
+    g.R2 = upload(p, R2);
+    g.C2 = upload(p, C2);
+    g.cpos = upload(p, cpos);
+    g.cph = upload(p, cph);
+    g.sph = upload(p, sph);
+    g.rho = upload(p, rho);
+    g.snode = upload(p, sn);
+    g.ctn = upload(p, ctn);
+    g.stn = upload(p, stn);
+    g.cpn = upload(p, cpn);
+    g.spn = upload(p, spn);
+    g.snode64 = upload(p, sn64);
+    g.tnode64 = upload(p, tn64);
+    g.pnode64 = upload(p, pn64);
+    // Centred-factor phase of the box-centre offset (kappa H_d sqrt(m)) mod 2 pi, m = |k_A - k_B|^2.
+    std::vector<float> ph(28);
+    for (int m = 0; m < 28; ++m) ph[m] = (float)std::fmod(p.kappa * Hd * std::sqrt((double)m), 2.0 * M_PI);
+    p.L[d].phtab = upload(p, ph);
+    p.L[d].host_grid = {ns, nt, np};
+    (void)keep;
+}
+
+template <class T>
+T read_one(Plan& p, const T* d) {
+    T h;
+    IFGF_CUDA(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, p.stream));
+    IFGF_CUDA(cudaStreamSynchronize(p.stream));
+    return h;
+}
+
+__global__ void k_dup_check(const double* __restrict__ Xs, int64_t N, const uint64_t* __restrict__ keys,
+                            int* __restrict__ flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    // Coincident points share their level-21 key, and equal keys are contiguous.
+    for (int64_t j = i + 1; j < N && keys[j] == keys[i]; ++j)
+        if (Xs[i] == Xs[j] && Xs[N + i] == Xs[N + j] && Xs[2 * N + i] == Xs[2 * N + j]) atomicExch(flag, 1);
+}
+
+}  // namespace
+
+void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
+    const int64_t N = p.N;
+    cudaStream_t s = p.stream;
+
+    // Root cube.
+    const int nb = (int)std::min<int64_t>(1024, (N + kThreads - 1) / kThreads);
+    double* part = dalloc<double>(p, (size_t)nb * 7);
+    IFGF_LAUNCH(k_bbox_partial, nb, kThreads, 0, s, X, N, part);
+    std::vector<double> hp((size_t)nb * 7);
+    IFGF_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb * 7, cudaMemcpyDeviceToHost, s));
+    IFGF_CUDA(cudaStreamSynchronize(s));
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = 0; b < nb; ++b) {
+        if (hp[b * 7 + 6] != 0.0) fail(IFGF_ERR_INVALID_ARG, "non-finite coordinate");
+        for (int c = 0; c < 3; ++c) {
+            mn[c] = std::min(mn[c], hp[b * 7 + c]);
+            mx[c] = std::max(mx[c], hp[b * 7 + 3 + c]);
+        }
+    }
+    double ext = 0.0;
+    for (int c = 0; c < 3; ++c) ext = std::max(ext, mx[c] - mn[c]);
+    if (!(ext > 0.0)) fail(IFGF_ERR_INVALID_ARG, "all points coincide");
+    p.H1 = ext * (1.0 + std::ldexp(1.0, -20));
+    for (int c = 0; c < 3; ++c) p.a[c] = 0.5 * (mn[c] + mx[c]) - 0.5 * p.H1;
+
+    // Morton keys and the sorted order (ties by the caller's index: the sort is stable).
+    p.key = dalloc<uint64_t>(p, N);
+    p.perm = dalloc<int32_t>(p, N);
+    IFGF_LAUNCH(k_keys, grid_for(N, kThreads), kThreads, 0, s, X, N, p.a[0], p.a[1], p.a[2], p.H1, p.key, p.perm);
+    radix_sort_pairs(p, p.key, p.perm, N, 3 * (kKeyLevel - 1));
+    p.Xs = dalloc<double>(p, 3 * (size_t)N);
+    IFGF_LAUNCH(k_gather_points, grid_for(N, kThreads), kThreads, 0, s, X, N, p.perm, p.Xs);
+
+    // Boxes per level.
+    uint8_t* d0 = dalloc<uint8_t>(p, N);
+    unsigned long long* hist = dalloc<unsigned long long>(p, 24);
+    IFGF_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 24, s));
+    IFGF_LAUNCH(k_level_split, grid_for(N, kThreads), kThreads, 0, s, p.key, N, d0, hist);
+    unsigned long long hh[24];
+    IFGF_CUDA(cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, s));
+    int* dflag = dalloc<int>(p, 1);
+    IFGF_CUDA(cudaMemsetAsync(dflag, 0, sizeof(int), s));
+    IFGF_LAUNCH(k_dup_check, grid_for(N, kThreads), kThreads, 0, s, p.Xs, N, p.key, dflag);
+    int dup = 0;
+    IFGF_CUDA(cudaMemcpyAsync(&dup, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IFGF_CUDA(cudaStreamSynchronize(s));
+    if (dup) fail(IFGF_ERR_INVALID_ARG, "two points share all three coordinates");
+    int64_t nd[kMaxLevel + 2];
+    {
+        int64_t acc = 1;
+        for (int d = 1; d <= kMaxLevel; ++d) {
+            acc += (int64_t)hh[d];
+            nd[d] = acc;
+        }
+    }
+    int D = levels;
+    if (D == 0) {
+        D = kMaxLevel;
+        for (int d = 3; d <= kMaxLevel; ++d)
+            if (N <= (int64_t)opt.leaf_target * nd[d]) {
+                D = d;
+                break;
+            }
+    }
+    p.D = D;
+    p.u = std::ldexp(p.H1, -D);
+
+    int32_t* flag = dalloc<int32_t>(p, N);
+    int32_t* pos = dalloc<int32_t>(p, N);
+    for (int d = 1; d <= D; ++d) p.L[d].n = (int32_t)nd[d];
+    for (int d = 1; d <= D; ++d) {
+        Level& L = p.L[d];
+        L.start = dalloc<int32_t>(p, (size_t)L.n + 1);
+        L.key = dalloc<uint64_t>(p, L.n);
+        L.k = dalloc<int4>(p, L.n);
+        L.pbox = dalloc<int32_t>(p, N);
+        IFGF_LAUNCH(k_level_flags, grid_for(N, kThreads), kThreads, 0, s, d0, N, d, flag);
+        exclusive_scan_i32(p, flag, pos, N);
+        IFGF_LAUNCH(k_level_boxes, grid_for(N, kThreads), kThreads, 0, s, flag, pos, p.key, N, d, L.n, L.start, L.key,
+                    L.k, L.pbox);
+    }
+    dfree_ptr(p, flag);
+    dfree_ptr(p, pos);
+    dfree_ptr(p, d0);
+    dfree_ptr(p, hist);
+    dfree_ptr(p, dflag);
+    dfree_ptr(p, part);
+    for (int d = 1; d <= D; ++d) {
+        Level& L = p.L[d];
+        L.parent = dalloc<int32_t>(p, L.n);
+        IFGF_LAUNCH(k_parents, grid_for(L.n, kThreads), kThreads, 0, s, L.start, L.n, d > 1 ? p.L[d - 1].pbox : nullptr,
+                    L.parent);
+    }
+    for (int d = 1; d <= D; ++d) {
+        Level& L = p.L[d];
+        L.cstart = dalloc<int32_t>(p, (size_t)L.n + 1);
+        if (d < D)
+            IFGF_LAUNCH(k_child_start, grid_for(p.L[d + 1].n, kThreads), kThreads, 0, s, p.L[d + 1].parent,
+                        p.L[d + 1].n, L.n, L.cstart);
+        else
+            IFGF_CUDA(cudaMemsetAsync(L.cstart, 0, sizeof(int32_t) * ((size_t)L.n + 1), s));
+    }
+    p.off = dalloc<float4>(p, N);
+    IFGF_LAUNCH(k_offsets, grid_for(N, kThreads), kThreads, 0, s, p.Xs, N, p.a[0], p.a[1], p.a[2], p.H1,
+                std::ldexp(1.0, D), p.L[D].pbox, p.L[D].k, p.off);
+
+    // Neighbours (levels 2..D) and cousins (levels 3..D).
+    for (int d = 2; d <= D; ++d) {
+        Level& L = p.L[d];
+        L.nnb = dalloc<int32_t>(p, L.n);
+        L.nb = dalloc<int32_t>(p, (size_t)L.n * kMaxNbr);
+        IFGF_LAUNCH(k_neighbours, grid_for(L.n, kThreads), kThreads, 0, s, L.key, L.k, L.n, d, L.nnb, L.nb);
+    }
+    for (int d = 3; d <= D; ++d) {
+        Level& L = p.L[d];
+        Level& Lp = p.L[d - 1];
+        L.ncs = dalloc<int32_t>(p, L.n);
+        L.cs = dalloc<int32_t>(p, (size_t)L.n * kMaxCous);
+        IFGF_LAUNCH(k_cousins, grid_for(L.n, kThreads), kThreads, 0, s, L.k, L.parent, L.n, Lp.nnb, Lp.nb, Lp.cstart,
+                    L.ncs, L.cs);
+    }
+
+    // Cone grids and the relevant cones, top-down d = 3..D (level d needs level d-1).
+    std::vector<std::vector<char>> keep;
+    for (int d = 3; d <= D; ++d) build_grid(p, d, opt, keep);
+    for (int d = 3; d <= D; ++d) {
+        Level& L = p.L[d];
+        const int64_t total = (int64_t)L.n * L.g.C;
+        if (total >= ((int64_t)1 << 31)) fail(IFGF_ERR_UNSUPPORTED, "dense cone table exceeds 2^31 entries");
+        L.slot = dalloc<int32_t>(p, total);
+        IFGF_CUDA(cudaMemsetAsync(L.slot, 0, sizeof(int32_t) * total, s));
+        IFGF_LAUNCH(k_mark_cousin_points, grid_for(N, kThreads), kThreads, 0, s, N, D, d, L.pbox, p.L[D].pbox,
+                    p.L[D].k, L.k, L.ncs, L.cs, p.off, L.g, L.slot);
+        if (d > 3) {
+            Level& Lp = p.L[d - 1];
+            if (Lp.nc > 0)
+                IFGF_LAUNCH(k_mark_parent_nodes, grid_for(Lp.nc * p.P, kThreads), kThreads, 0, s, Lp.nc, p.P, p.Ps,
+                            p.Pt, p.Pp, D, d, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, Lp.g, L.g, L.slot);
+        }
+        int32_t* cpos = dalloc<int32_t>(p, total);
+        exclusive_scan_i32(p, L.slot, cpos, total);
+        const int32_t last_pos = read_one(p, cpos + (total - 1));
+        const int32_t last_flag = read_one(p, L.slot + (total - 1));
+        L.nc = (int64_t)last_pos + last_flag;
+        L.cone_box = dalloc<int32_t>(p, L.nc);
+        L.cone_gam = dalloc<int32_t>(p, L.nc);
+        IFGF_LAUNCH(k_finalize_cones, grid_for(total, kThreads), kThreads, 0, s, L.slot, cpos, total, L.g.C,
+                    L.cone_box, L.cone_gam);
+        dfree_ptr(p, cpos);
+    }
+}
+
+}  // namespace ifgf

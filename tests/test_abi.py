@@ -1,0 +1,76 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that include/ifgf.h declares.
+
+No compute call is made here (no GPU on this host): only host-side functions that touch no
+device (option defaults, status strings) are called.
+"""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "ifgf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(ifgf_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import paper_2112_15198_gb300 as ifgf
+
+    return ifgf.load(build=True)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("ifgf_plan_create", "ifgf_apply", "ifgf_plan_destroy", "ifgf_plan_query"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_host_only_helpers(lib):
+    import paper_2112_15198_gb300 as ifgf
+
+    opt = ifgf.Options()
+    lib.ifgf_options_default(ctypes.byref(opt))
+    assert opt.struct_size == ctypes.sizeof(ifgf.Options)
+    assert tuple(opt.base_cones) == (2, 4, 8) and opt.leaf_target == 64 and opt.max_nrhs == 1
+    assert abs(opt.tau - 0.5) < 1e-15
+    assert lib.ifgf_status_string(0) == b"ok"
+    assert lib.ifgf_status_string(1) == b"invalid argument"
+
+
+def test_invalid_arguments_rejected_before_any_device_work(lib):
+    import paper_2112_15198_gb300 as ifgf
+
+    h = ctypes.c_void_p()
+    o = (ctypes.c_int32 * 3)(3, 5, 5)
+    # NULL points / N < 2 / negative kappa / bad levels: rejected by host-side validation
+    assert lib.ifgf_plan_create(None, 10, 1.0, o, 0, None, None, ctypes.byref(h)) == 1
+    assert lib.ifgf_plan_create(ctypes.c_void_p(16), 1, 1.0, o, 0, None, None, ctypes.byref(h)) == 1
+    assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, -1.0, o, 0, None, None, ctypes.byref(h)) == 1
+    assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, 1.0, o, 2, None, None, ctypes.byref(h)) == 1
+    bad = (ctypes.c_int32 * 3)(4, 4, 4)
+    assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, 1.0, bad, 0, None, None, ctypes.byref(h)) == 1
+    assert b"orders" in lib.ifgf_last_error()
+    assert lib.ifgf_plan_destroy(None) == 0
+    assert lib.ifgf_apply(None, None, 1, None, None) == 1
+
+
+def test_library_links_no_torch(lib):
+    import paper_2112_15198_gb300 as ifgf
+
+    data = open(ifgf.library_path(), "rb").read()
+    assert b"libtorch" not in data and b"libc10" not in data

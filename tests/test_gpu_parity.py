@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (written here, derived in the design doc):
+  - tree, interaction lists, cone lists: bit-exact (integer work);
+  - FP64 path vs CPU IFGF (same algorithm, FP64, different summation order): rel. L2 1e-10;
+  - mixed path vs CPU IFGF: rel. L2 3e-5 (FP32 arithmetic over D levels of interpolation);
+  - either path vs the direct sum of Eq. (1): the method's accuracy, rel. L2 2e-4 at the
+    default orders (the CPU IFGF itself measures ~1.1e-4 on the 4-wavelength sphere).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ifgf_inputs as W
+import oracle
+
+torch = pytest.importorskip("torch")
+ifgf = pytest.importorskip("paper_2112_15198_gb300")
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TREE_ITEMS = [
+    ("PERM", 0), ("KEYS", 0),
+]
+
+
+def _plan(pts, kappa, **kw):
+    return ifgf.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(DEV), kappa, **kw)
+
+
+def _apply(plan, dens, prec, **kw):
+    cdt = torch.complex64 if prec == "mixed" else torch.complex128
+    a = torch.from_numpy(np.atleast_2d(dens).astype(np.complex128)).to(DEV).to(cdt)
+    out = torch.empty_like(a)
+    plan.apply(a, out, **kw)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.complex128)
+
+
+def assert_same_tree(gp, op):
+    """Every integer list of the GPU plan equals the oracle's, bit for bit."""
+    assert gp.D == op.D
+    Qg, Qo = ifgf.Q, oracle
+    np.testing.assert_array_equal(gp.query(Qg.PERM), op.get(Qo.Q_PERM))
+    np.testing.assert_array_equal(gp.query(Qg.KEYS), op.get(Qo.Q_KEYS))
+    for d in range(1, gp.D + 1):
+        for qg, qo in ((Qg.BOX_KEYS, Qo.Q_BOX_KEYS), (Qg.BOX_START, Qo.Q_BOX_START), (Qg.BOX_PARENT, Qo.Q_BOX_PARENT)):
+            np.testing.assert_array_equal(gp.query(qg, d), op.get(qo, d), err_msg=f"item {qg} level {d}")
+        if d < gp.D:
+            np.testing.assert_array_equal(gp.query(Qg.CHILD_START, d), op.get(Qo.Q_CHILD_START, d))
+        if d >= 2:
+            np.testing.assert_array_equal(gp.query(Qg.NBR_COUNT, d), op.get(Qo.Q_NBR_COUNT, d))
+            np.testing.assert_array_equal(gp.query(Qg.NBR_LIST, d), op.get(Qo.Q_NBR_LIST, d))
+        if d >= 3:
+            np.testing.assert_array_equal(gp.query(Qg.COUS_COUNT, d), op.get(Qo.Q_COUS_COUNT, d))
+            np.testing.assert_array_equal(gp.query(Qg.COUS_LIST, d), op.get(Qo.Q_COUS_LIST, d))
+            assert gp.grid(d) == op.grid(d)
+            np.testing.assert_array_equal(gp.query(Qg.CONE_BOX, d), op.get(Qo.Q_CONE_BOX, d), err_msg=f"cones {d}")
+            np.testing.assert_array_equal(gp.query(Qg.CONE_GAMMA, d), op.get(Qo.Q_CONE_GAMMA, d), err_msg=f"cones {d}")
+
+
+CASES = {
+    "sphere4": lambda: (W.make("sphere4").points(), W.make("sphere4").kappa, {}),
+    "cloud_ragged": lambda: (W.random_cloud(1003, seed=5), 2 * math.pi * 3, {}),
+    "spheroid": lambda: (W.spheroid(20000, 0.5, 0.125, seed=9), 2 * math.pi * 6, {}),
+    "tiny": lambda: (W.random_cloud(7, seed=2), 1.0, {}),
+    "two_points": lambda: (np.array([[0.0, 1.0], [0.0, 0.5], [0.0, -0.25]]), 3.0, {}),
+    "one_leaf_D3": lambda: (W.random_cloud(40, seed=3), 2.0, {"levels": 3}),
+    "planar": lambda: (np.stack([W.random_cloud(3000, seed=4)[0], W.random_cloud(3000, seed=5)[1],
+                                 np.zeros(3000)]), 2 * math.pi * 4, {}),
+    "deep": lambda: (W.fibonacci_sphere(3000), 2 * math.pi * 2, {"levels": 7}),
+    "laplace": lambda: (W.fibonacci_sphere(12000), 0.0, {}),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_tree_and_cones_bit_exact(case):
+    pts, kappa, kw = CASES[case]()
+    op = oracle.Plan(pts, kappa, **kw)
+    gp = _plan(pts, kappa, **kw)
+    assert_same_tree(gp, op)
+
+
+@pytest.mark.parametrize("case", ["sphere4", "cloud_ragged", "spheroid", "two_points", "one_leaf_D3", "planar",
+                                  "deep", "laplace"])
+def test_fp64_matches_cpu_ifgf(case):
+    pts, kappa, kw = CASES[case]()
+    n = pts.shape[1]
+    dens = W.densities(n, 1, 17)
+    ref = oracle.Plan(pts, kappa, **kw).apply(dens)
+    gp = _plan(pts, kappa, precision="fp64", **kw)
+    got = _apply(gp, dens, "fp64")
+    assert gp.status() == 0
+    assert oracle.rel_l2(got, ref) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["sphere4", "cloud_ragged", "spheroid", "two_points", "one_leaf_D3", "planar",
+                                  "deep", "laplace"])
+def test_mixed_matches_cpu_ifgf(case):
+    pts, kappa, kw = CASES[case]()
+    n = pts.shape[1]
+    dens = W.densities(n, 1, 17)
+    ref = oracle.Plan(pts, kappa, **kw).apply(dens)
+    gp = _plan(pts, kappa, precision="mixed", **kw)
+    got = _apply(gp, dens, "mixed")
+    assert gp.status() == 0
+    assert oracle.rel_l2(got, ref) < 3e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("stage", ["near", "leaf_level", "top_level"])
+def test_stages_match_cpu_ifgf(prec, stage):
+    w = W.make("sphere4")
+    pts, kappa = w.points(), w.kappa
+    dens = w.densities()
+    op = oracle.Plan(pts, kappa)
+    gp = _plan(pts, kappa, precision=prec)
+    near, mask = {"near": (True, 0), "leaf_level": (False, 1 << op.D), "top_level": (False, 1 << 3)}[stage]
+    ref = op.apply(dens, near=near, level_mask=mask)
+    got = _apply(gp, dens, prec, near=near, level_mask=mask)
+    tol = 1e-10 if prec == "fp64" else 3e-5
+    assert oracle.rel_l2(got, ref) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_accuracy_vs_direct_sum_sphere4(prec):
+    w = W.make("sphere4")
+    pts, kappa = w.points(), w.kappa
+    dens = w.densities()
+    exact = oracle.direct_sum(pts, kappa, dens)
+    got = _apply(_plan(pts, kappa, precision=prec), dens, prec)
+    assert oracle.rel_l2(got, exact) < 2e-4
+
+
+def test_multiple_rhs_and_determinism():
+    pts = W.fibonacci_sphere(6000)
+    kappa = 2 * math.pi * 3
+    A = W.densities(6000, 3, 5)
+    for prec in ("fp64", "mixed"):
+        gp = _plan(pts, kappa, precision=prec, max_nrhs=3)
+        all3 = _apply(gp, A, prec)
+        again = _apply(gp, A, prec)
+        assert np.array_equal(all3, again)  # no float atomics: bitwise reproducible
+        for r in range(3):
+            one = _apply(gp, A[r], prec)[0]
+            assert np.array_equal(one, all3[r])
+
+
+def test_higher_orders_fp64():
+    pts = W.fibonacci_sphere(3000)
+    kappa = 2 * math.pi * 2
+    dens = W.densities(3000, 1, 3)
+    op = oracle.Plan(pts, kappa, orders=(5, 7, 7), levels=4)
+    gp = _plan(pts, kappa, precision="fp64", orders=(5, 7, 7), levels=4)
+    assert_same_tree(gp, op)
+    assert oracle.rel_l2(_apply(gp, dens, "fp64"), op.apply(dens)) < 1e-10
+    exact = oracle.direct_sum(pts, kappa, dens)
+    assert oracle.rel_l2(_apply(gp, dens, "fp64"), exact) < 2e-6
+
+
+@pytest.mark.parametrize("what", ["duplicate", "nan", "n1", "kappa", "levels", "orders", "host_points"])
+def test_invalid_input_rejected(what):
+    pts = W.random_cloud(100, seed=1)
+    kw = {}
+    kappa = 1.0
+    if what == "duplicate":
+        pts[:, 10] = pts[:, 50]
+    elif what == "nan":
+        pts[1, 3] = np.nan
+    elif what == "n1":
+        pts = pts[:, :1]
+    elif what == "kappa":
+        kappa = -1.0
+    elif what == "levels":
+        kw["levels"] = 22
+    elif what == "orders":
+        kw["orders"] = (4, 4, 4)
+    with pytest.raises(ifgf.IFGFError) as e:
+        if what == "host_points":
+            ifgf.Plan(torch.from_numpy(pts), kappa)
+        else:
+            _plan(pts, kappa, **kw)
+    assert e.value.status == 1
+
+
+def test_nrhs_limit():
+    pts = W.random_cloud(500, seed=1)
+    gp = _plan(pts, 1.0, max_nrhs=2)
+    a = torch.zeros((3, 500), dtype=torch.complex64, device=DEV)
+    with pytest.raises(ifgf.IFGFError):
+        gp.apply(a, torch.empty_like(a))
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_full_size_sphere64_sampled(prec):
+    """The 64-wavelength, 1,572,864-point sphere in the bench's configuration: error on 2,000
+    seeded targets against the direct sum, and the tree/cone lists against the oracle's."""
+    w = W.make("sphere64")
+    pts, kappa = w.points(), w.kappa
+    dens = w.densities()
+    tgt = w.targets()
+    exact = oracle.direct_sum(pts, kappa, dens, tgt)
+    gp = _plan(pts, kappa, precision=prec)
+    got = _apply(gp, dens, prec)[:, tgt]
+    assert gp.status() == 0
+    err = oracle.rel_l2(got, exact)
+    print(f"sphere64 {prec}: rel. L2 error on {len(tgt)} targets = {err:.3e}")
+    assert err < 5e-4
+    if prec == "mixed":
+        op = oracle.Plan(pts, kappa)
+        assert_same_tree(gp, op)
