@@ -121,6 +121,8 @@ class Workload:
 WORKLOADS = {
     # Plain FP64 case: 4-wavelength sphere, every point is a target.
     "sphere4": Workload("sphere4", "sphere", 24_576, 4.0, 1, 1, 24_576),
+    # Same sampling density at a quarter of the points (profiling-sized case).
+    "sphere32": Workload("sphere32", "sphere", 393_216, 32.0, 1, 6, 2000),
     # Headline case: 64-wavelength sphere, single density.
     "sphere64": Workload("sphere64", "sphere", 1_572_864, 64.0, 1, 2, 2000),
     # Oblate spheroid (a, a, a/4), 128 wavelengths, 32 densities.
