@@ -161,6 +161,37 @@ int64_t ifgf_launch_count(void);
 void ifgf_timing_enable(int32_t on);
 ifgf_status ifgf_timing_collect(double* ms, int64_t* launches);
 
+/*
+ * Allocation-free Morton order of N points.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the order, because
+ * their device memory is wholly owned by another allocator (a framework's caching pool or an
+ * arena reserved up front) or because cudaMalloc/cudaFree, which can synchronise the device
+ * and fail under memory pressure, are not acceptable in their loop.
+ *
+ * It computes what ifgf_plan_create computes first: the root cube, the level-21 Morton keys
+ * and the stable key sort (ties by the caller's index), so perm and keys equal
+ * IFGF_Q_PERM / IFGF_Q_KEYS of a plan built from the same points.
+ *
+ *   points  device, 3*N doubles, x[0..N), y[0..N), z[0..N).  Read only.
+ *   N       2 <= N <= IFGF_NOALLOC_MAX_POINTS; larger N returns IFGF_ERR_INVALID_ARG.
+ *   perm    device, int32[N], output: sorted position -> caller index.
+ *   keys    device, uint64[N], output: sorted keys.
+ *   stream  cudaStream_t as void*.
+ *
+ * Memory: it calls no allocation routine.  Its scratch is one static device array of
+ * about 12.6 MB (second sort buffers for 2^20 points, digit histograms, bounding-box partials)
+ * that every device which loads this library holds until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current); make that first call before any stream capture.  All calls share the array and
+ * each call overwrites what it reads, so calls that overlap on the GPU (two streams, or two
+ * host threads) race and must be serialised by the caller.  The call returns after the
+ * bounding box has been read back to the host; the keys and the sort are queued on `stream`.
+ * Errors: IFGF_ERR_INVALID_ARG (NULL pointer, N out of range, non-finite coordinate, all
+ * points coincident), IFGF_ERR_CUDA.
+ */
+#define IFGF_NOALLOC_MAX_POINTS (1 << 20)
+ifgf_status ifgf_morton_order_noalloc(const double* points, int64_t N, int32_t* perm, uint64_t* keys, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
