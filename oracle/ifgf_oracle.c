@@ -25,7 +25,8 @@
  *     h_d = sqrt(3)/2 H_d (box circumradius), s in [0, eta], eta = sqrt(3)/3;
  *   - uniform cone grids (n_s, n_theta, n_phi) per level: a base grid, doubled in
  *     all three directions e_d times, e_d the smallest e >= 0 with
- *     kappa*H_d <= 2*pi*tau*2^e (boxes of at most tau*2^e wavelengths);
+ *     kappa*H_d <= 2*pi*tau*2^e*(1 + 2^-10) (boxes of at most tau*2^e wavelengths, with a
+ *     margin for the 2^-20 enlargement of the root cube);
  *   - tensor-product Chebyshev interpolation on first-kind nodes of orders
  *     (P_s, P_theta, P_phi); "generate interpolant" = Chebyshev coefficients by
  *     discrete cosine orthogonality;
@@ -599,13 +600,15 @@ orc_plan* orc_plan_create(int64_t N, const double* x, const double* y, const dou
     p->Wp = cheb_analysis(Pp);
 
     /* Cone grids: the base grid, doubled in all three directions e_d times, where e_d is the
-     * smallest e >= 0 with kappa*H_d <= 2 pi tau 2^e (boxes of at most tau*2^e wavelengths).
+     * smallest e >= 0 with kappa*H_d <= 2 pi tau 2^e (1 + 2^-10) (boxes of at most tau*2^e
+     * wavelengths; the margin keeps the 2^-20 enlargement of the root cube from tipping a box
+     * whose side is tau*2^e wavelengths into the next grid).
      * Above tau wavelengths each level up thus splits every cone into eight (Sec. 3.3). */
     const double eta = sqrt(3.0) / 3.0;
     for (int d = D; d >= 3; --d) {
         double Hd = ldexp(p->H1, 1 - d);
         int e = 0;
-        while (kappa > 0.0 && e < 24 && kappa * Hd > 2.0 * M_PI * tau * ldexp(1.0, e)) ++e;
+        while (kappa > 0.0 && e < 24 && kappa * Hd > 2.0 * M_PI * tau * ldexp(1.0, e) * (1.0 + ldexp(1.0, -10))) ++e;
         int gns = bns << e, gnt = bnt << e, gnp = bnp << e;
         orc_grid* g = &p->L[d].g;
         g->ns = gns; g->nt = gnt; g->np = gnp;

@@ -251,51 +251,153 @@ __device__ __forceinline__ float3 node_grid(const LevelGrid& gp, int Ps, int Pt,
 //   F_j(x) = sum over relevant children B_k of B_j of I_P C_{k;alpha}(x) G(x,x_k)/G(x,x_j),
 //   G(x,x_k)/G(x,x_j) = (r_j/r_k) exp(i kappa (r_k - r_j)),  r_k - r_j = (|o|^2 - 2 q.o)/(r_k + r_j),
 // q the node offset from x_j and o the child-centre offset; then the parent interpolant.
+// Block work layout: kPropCones consecutive parent cones; the (cone, child, node) evaluations
+// of the block are flattened over its threads (no idle lanes beyond the last round); node
+// offsets are staged in shared memory; values are summed over children in child order, then
+// the parent interpolants are generated.
+constexpr int kPropCones = 4;
+constexpr int kPropThreads = 256;
+
 template <int PS, int PT, int PP>
-__global__ void k_prop_f32(const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
-                           const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
-                           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
-                           const float2* __restrict__ cchild, float2* __restrict__ cparent, int sh, float ku,
-                           const float* __restrict__ W, int cstride, int nrhs, int* __restrict__ status) {
+__global__ void __launch_bounds__(kPropThreads, 5)
+k_prop_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
+           const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
+           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
+           const float2* __restrict__ cchild, float2* __restrict__ cparent, int sh, float ku,
+           const float* __restrict__ W, int cstride, int nrhs, int* __restrict__ status) {
     constexpr int P = PS * PT * PP;
-    __shared__ float2 f[P], tmp[P];
-    const int pc = blockIdx.x;
+    constexpr int NC = kPropCones;
+    __shared__ float2 vals[NC][8][P];
+    __shared__ float4 qn[NC][P];
+    __shared__ float2 f[NC][P], tmp[NC][P];
+    __shared__ int s_off[NC + 1], s_kb0[NC], s_jb[NC];
+    const int tid = threadIdx.x;
     const int r = blockIdx.y;
-    const int n = threadIdx.x;
-    if (n < P) {
-        const int jb = pcone_box[pc];
-        const float3 q = node_grid(gp, PS, PT, PP, pcone_gam[pc], n);
-        const float rj = sqrtf(fmaf(q.x, q.x, fmaf(q.y, q.y, q.z * q.z)));
-        const int4 kj = kp[jb];
-        const float oo = 3.0f * (float)(1 << sh) * (float)(1 << sh);
-        float2 acc = make_float2(0.f, 0.f);
-        const int k1 = pcstart[jb + 1];
-        for (int kb = pcstart[jb]; kb < k1; ++kb) {
-            const int4 kk = kd[kb];
-            const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
-            const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
-            const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
-            const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
-            const int s = __ldg(&slot[(int64_t)kb * g.C + cl.gamma]);
-            if (s < 0) {
-                set_status(status, IFGF_ERR_INTERNAL);
-                continue;
+    const int64_t pc0 = (int64_t)blockIdx.x * NC;
+    if (tid == 0) {
+        int acc = 0;
+        for (int c = 0; c < NC; ++c) {
+            s_off[c] = acc;
+            const int64_t pc = pc0 + c;
+            if (pc < ncp) {
+                const int jb = pcone_box[pc];
+                s_jb[c] = jb;
+                s_kb0[c] = pcstart[jb];
+                acc += (pcstart[jb + 1] - pcstart[jb]) * P;
+            } else {
+                s_jb[c] = -1;
+                s_kb0[c] = 0;
             }
-            const float2 F = interp_f32<PS, PT, PP>(cchild + ((int64_t)s * nrhs + r) * cstride, cl.ts, cl.tt, cl.tp);
-            const float qo = fmaf(q.x, ox, fmaf(q.y, oy, q.z * oz));
-            const float dr = __fdividef(fmaf(-2.f, qo, oo), cl.r + rj);
-            const float2 e = cis_f32(ku * dr);
-            const float w = __fdividef(rj, cl.r);
-            const float2 ratio = make_float2(e.x * w, e.y * w);
-            const float2 t = cmul(F, ratio);
-            acc.x += t.x;
-            acc.y += t.y;
         }
-        f[n] = acc;
+        s_off[NC] = acc;
+    }
+    // node offsets from the parent centre (grid units, the plan's exact products) and |q|
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int64_t pc = pc0 + c;
+        if (pc < ncp) {
+            const int gam = pcone_gam[pc];
+            const int ip = gam % gp.np, it = (gam / gp.np) % gp.nt, is = gam / (gp.np * gp.nt);
+            const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+            const float rho = gp.rho[is * PS + qa];
+            const float st = gp.stn[it * PT + qb], ct = gp.ctn[it * PT + qb];
+            const float cp = gp.cpn[ip * PP + qc], sp = gp.spn[ip * PP + qc];
+            const float qx = __fmul_rn(rho, __fmul_rn(st, cp)), qy = __fmul_rn(rho, __fmul_rn(st, sp));
+            const float qz = __fmul_rn(rho, ct);
+            qn[c][n] = make_float4(qx, qy, qz, sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz))));
+        }
     }
     __syncthreads();
-    const float2 c = cheb_coeffs_smem<PS, PT, PP>(f, tmp, W, n);
-    if (n < P) cparent[((int64_t)pc * nrhs + r) * cstride + n] = c;
+    const float oo = 3.0f * (float)(1 << sh) * (float)(1 << sh);
+    const int total = s_off[NC];
+    for (int item = tid; item < total; item += kPropThreads) {
+        int c = 0;
+#pragma unroll
+        for (int k = 1; k < NC; ++k) c += item >= s_off[k];
+        const int rem = item - s_off[c];
+        const int ch = rem / P, n = rem - ch * P;
+        const int kb = s_kb0[c] + ch;
+        const int4 kj = kp[s_jb[c]];
+        const int4 kk = kd[kb];
+        const float4 q = qn[c][n];
+        const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
+        const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
+        const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
+        const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
+        const int s = __ldg(&slot[(int64_t)kb * g.C + cl.gamma(g)]);
+        float2 t = make_float2(0.f, 0.f);
+        if (s < 0) {
+            set_status(status, IFGF_ERR_INTERNAL);
+        } else {
+            const float2 F = interp_f32<PS, PT, PP>(cchild + ((int64_t)s * nrhs + r) * cstride, cl.ts, cl.tt, cl.tp);
+            // G(x,x_k)/G(x,x_j) = (r_j/r_k) exp(i kappa (r_k - r_j)), r_k - r_j = (|o|^2 - 2 q.o)/(r_k + r_j)
+            const float qo = fmaf(q.x, ox, fmaf(q.y, oy, q.z * oz));
+            const float dr = __fdividef(fmaf(-2.f, qo, oo), cl.r + q.w);
+            const float2 e = cis_f32(ku * dr);
+            const float w = __fdividef(q.w, cl.r);
+            t = cmul(F, make_float2(e.x * w, e.y * w));
+        }
+        vals[c][ch][n] = t;
+    }
+    __syncthreads();
+    // sum over children in child order, then the Chebyshev coefficients (phi, theta, s passes)
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int nch = (s_off[c + 1] - s_off[c]) / P;
+        float2 a = make_float2(0.f, 0.f);
+        for (int ch = 0; ch < nch; ++ch) {
+            a.x += vals[c][ch][n].x;
+            a.y += vals[c][ch][n].y;
+        }
+        f[c][n] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* row = &f[c][(qa * PT + qb) * PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const float w = Wp[qc * PP + k];
+            acc.x = fmaf(w, row[k].x, acc.x);
+            acc.y = fmaf(w, row[k].y, acc.y);
+        }
+        tmp[c][n] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < PT; ++j) {
+            const float w = Wt[qb * PT + j];
+            const float2 v = tmp[c][(qa * PT + j) * PP + qc];
+            acc.x = fmaf(w, v.x, acc.x);
+            acc.y = fmaf(w, v.y, acc.y);
+        }
+        f[c][n] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int64_t pc = pc0 + c;
+        if (pc >= ncp) continue;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const float w = Ws[qa * PS + i];
+            const float2 v = f[c][(i * PT + qb) * PP + qc];
+            acc.x = fmaf(w, v.x, acc.x);
+            acc.y = fmaf(w, v.y, acc.y);
+        }
+        cparent[(pc * nrhs + r) * cstride + n] = acc;
+    }
 }
 
 template <int PS, int PT, int PP>
@@ -329,15 +431,15 @@ __global__ void k_prop_f64(const int32_t* __restrict__ pcone_box, const int32_t*
             const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
             const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
             const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
-            const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
-            const int sl = slot[(int64_t)kb * g.C + cl.gamma];
+            const int gam = classify_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
+            const int sl = slot[(int64_t)kb * g.C + gam];
             if (sl < 0) {
                 set_status(status, IFGF_ERR_INTERNAL);
                 continue;
             }
             const double xk = a0 + (kk.x + 0.5) * Hd, yk = a1 + (kk.y + 0.5) * Hd, zk = a2 + (kk.z + 0.5) * Hd;
             double ts, tt, tp, rk;
-            local_f64(g, cl.gamma, yx - xk, yy - yk, yz - zk, ts, tt, tp, rk);
+            local_f64(g, gam, yx - xk, yy - yk, yz - zk, ts, tt, tp, rk);
             const double2 F = interp_f64<PS, PT, PP>(cchild + ((int64_t)sl * nrhs + r) * cstride, ts, tt, tp);
             double sn, cs;
             sincos(kappa * (rk - rj), &sn, &cs);
@@ -386,7 +488,7 @@ __global__ void k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
         const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
         const ConeLocal cl = locate_f32(g, vx, vy, vz);
-        const int s = __ldg(&slot[(int64_t)B * g.C + cl.gamma]);
+        const int s = __ldg(&slot[(int64_t)B * g.C + cl.gamma(g)]);
         if (s < 0) {
             set_status(status, IFGF_ERR_INTERNAL);
             continue;
@@ -431,15 +533,15 @@ __global__ void k_interp_f64(int64_t N, int sh, const int32_t* __restrict__ pbox
         const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
         const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
-        const ConeLocal cl = locate_f32(g, vx, vy, vz);
-        const int s = slot[(int64_t)B * g.C + cl.gamma];
+        const int gam = classify_f32(g, vx, vy, vz);
+        const int s = slot[(int64_t)B * g.C + gam];
         if (s < 0) {
             set_status(status, IFGF_ERR_INTERNAL);
             continue;
         }
         const double xb = a0 + (kb.x + 0.5) * Hd, yb = a1 + (kb.y + 0.5) * Hd, zb = a2 + (kb.z + 0.5) * Hd;
         double ts, tt, tp, rr;
-        local_f64(g, cl.gamma, xi - xb, yi - yb, zi - zb, ts, tt, tp, rr);
+        local_f64(g, gam, xi - xb, yi - yb, zi - zb, ts, tt, tp, rr);
         const double2 F = interp_f64<PS, PT, PP>(coef + ((int64_t)s * nrhs + r) * cstride, ts, tt, tp);
         double sn, c;
         sincos(kappa * rr, &sn, &c);
@@ -506,9 +608,10 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
             if (Lp.nc > 0)
                 {
                     TimedScope ts_(TK_PROP, s);
-                    IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)Lp.nc, nrhs), BT, 0, s, Lp.cone_box, Lp.cone_gam,
-                                Lp.k, Lp.cstart, Lp.g, L.k, L.slot, L.g, (const float2*)p.coef[cur],
-                                (float2*)p.coef[1 - cur], sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
+                    IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((Lp.nc + kPropCones - 1) / kPropCones), nrhs),
+                                kPropThreads, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, Lp.g, L.k, L.slot,
+                                L.g, (const float2*)p.coef[cur], (float2*)p.coef[1 - cur], sh, ku, p.Wf, p.cstride,
+                                nrhs, p.d_status);
                 }
             cur = 1 - cur;
         }

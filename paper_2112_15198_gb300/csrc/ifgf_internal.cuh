@@ -191,79 +191,111 @@ __device__ __forceinline__ float rn_r2(float vx, float vy, float vz) {
 
 // Exact cone classification of an FP32 grid-unit offset v (r2 = rn_r2(v)).  Each bin index
 // is the number of edges the point lies on or beyond, decided by correctly rounded FP32
-// products/sums and comparisons; (cs, ct, cp) are candidate bins from approximate spherical
-// coordinates, from which the exact count is reached by stepping across edges (the edge
-// predicates are monotone in the edge index).
+// products/sums and comparisons; (is, it, ip) enter as candidate bins from approximate
+// spherical coordinates and leave as the exact counts, reached by stepping across edges (the
+// edge predicates are monotone in the edge index).
 //   s:     edge i (1 <= i < ns) passed iff r2 <= R2[i]                 (s >= i ds)
 //   theta: edge i (1 <= i < nt) passed iff vz <= cos(theta_i) r, in squared form
 //   phi:   edge j (1 <= j < np) passed iff phi >= phi_j, from the half plane left of edge j
 //          and the lower half plane H; 0 on the z axis.
-__device__ __forceinline__ int classify_exact(const LevelGrid& g, float vx, float vy, float vz, float r2, int cs,
-                                              int ct, int cp) {
-    int is = min(max(cs, 0), g.ns - 1);
+__device__ __forceinline__ void classify_exact(const LevelGrid& g, float vx, float vy, float vz, float r2, int& is,
+                                               int& it, int& ip) {
+    is = min(max(is, 0), g.ns - 1);
     while (is > 0 && !(r2 <= __ldg(&g.R2[is]))) --is;
     while (is + 1 < g.ns && (r2 <= __ldg(&g.R2[is + 1]))) ++is;
 
     const float z2 = __fmul_rn(vz, vz);
     const bool zneg = vz < 0.0f;
-    int it = min(max(ct, 0), g.nt - 1);
+    it = min(max(it, 0), g.nt - 1);
     auto Q = [&](int i) -> bool {
-        float c2r = __fmul_rn(__ldg(&g.C2[i]), r2);
+        const float c2r = __fmul_rn(__ldg(&g.C2[i]), r2);
         return __ldg(&g.cpos[i]) ? (zneg || z2 <= c2r) : (zneg && z2 >= c2r);
     };
     while (it > 0 && !Q(it)) --it;
     while (it + 1 < g.nt && Q(it + 1)) ++it;
 
-    int ip = 0;
-    if (!(vx == 0.0f && vy == 0.0f)) {
-        const bool H = (vy < 0.0f) || (vy == 0.0f && vx < 0.0f);
-        auto GE = [&](int j) -> bool {
-            bool Lj = __fsub_rn(__fmul_rn(__ldg(&g.cph[j]), vy), __fmul_rn(__ldg(&g.sph[j]), vx)) >= 0.0f;
-            int j2 = 2 * j;
-            return j2 < g.np ? (Lj || H) : (j2 == g.np ? H : (Lj && H));
-        };
-        ip = min(max(cp, 0), g.np - 1);
-        while (ip > 0 && !GE(ip)) --ip;
-        while (ip + 1 < g.np && GE(ip + 1)) ++ip;
+    if (vx == 0.0f && vy == 0.0f) {
+        ip = 0;
+        return;
     }
-    return (is * g.nt + it) * g.np + ip;
+    const bool H = (vy < 0.0f) || (vy == 0.0f && vx < 0.0f);
+    auto GE = [&](int j) -> bool {
+        const bool Lj = __fsub_rn(__fmul_rn(__ldg(&g.cph[j]), vy), __fmul_rn(__ldg(&g.sph[j]), vx)) >= 0.0f;
+        const int j2 = 2 * j;
+        return j2 < g.np ? (Lj || H) : (j2 == g.np ? H : (Lj && H));
+    };
+    ip = min(max(ip, 0), g.np - 1);
+    while (ip > 0 && !GE(ip)) --ip;
+    while (ip + 1 < g.np && GE(ip + 1)) ++ip;
 }
 
-// Approximate spherical coordinates (FP32) of a grid-unit offset and the exact cone; returns
-// gamma and the local coordinates (t_s, t_theta, t_phi) in [-1, 1] (slightly beyond at edges).
+// atan2 for evaluation coordinates: octant symmetry reduces the argument to t in [0, 1], where
+// atan(t) = t P(t^2) with an odd polynomial of degree 15 fitted to atan by iteratively
+// reweighted least squares on Chebyshev nodes (near-minimax); max error 1.4e-7 rad in FP32.
+__device__ __forceinline__ float fast_atan2(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float u = t * t;
+    float p = -0.004054564982652664f;
+    p = fmaf(p, u, 0.021862955763936043f);
+    p = fmaf(p, u, -0.055912334471940994f);
+    p = fmaf(p, u, 0.0964219868183136f);
+    p = fmaf(p, u, -0.1390863060951233f);
+    p = fmaf(p, u, 0.19946566224098206f);
+    p = fmaf(p, u, -0.33329859375953674f);
+    p = fmaf(p, u, 0.9999993443489075f);
+    float r = p * t;
+    if (ay > ax) r = 1.57079632679489662f - r;
+    if (x < 0.0f) r = 3.14159265358979324f - r;
+    return copysignf(r, y);
+}
+
+// Cone of a grid-unit offset v (exact bins) and its local coordinates (t_s, t_theta, t_phi)
+// in [-1, 1] (slightly beyond near edges), from approximate spherical coordinates.
 struct ConeLocal {
-    int gamma;
+    int is, it, ip;
     float ts, tt, tp;
     float r;  // |v| (approximate)
+    __device__ __forceinline__ int gamma(const LevelGrid& g) const { return (is * g.nt + it) * g.np + ip; }
 };
 
 __device__ __forceinline__ ConeLocal locate_f32(const LevelGrid& g, float vx, float vy, float vz) {
     const float r2 = rn_r2(vx, vy, vz);
     const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
     const float s = g.hg * rinv;
-    const float rxy = sqrtf(fmaf(vx, vx, vy * vy));
-    const float th = atan2f(rxy, vz);
-    float ph = atan2f(vy, vx);
+    const float rxy2 = fmaf(vx, vx, vy * vy);
+    const float rxy = rxy2 > 0.0f ? rxy2 * rsqrtf(rxy2) : 0.0f;
+    const float th = fast_atan2(rxy, vz);
+    float ph = fast_atan2(vy, vx);
     if (ph < 0.0f) ph += 6.28318530717958647692f;
-    const int cs = (int)(s * g.s_scale);
-    const int ct = (int)(th * g.t_scale);
-    const int cp = (int)(ph * g.p_scale);
-    const int gam = classify_exact(g, vx, vy, vz, r2, cs, ct, cp);
-    const int ip = gam % g.np;
-    const int it = (gam / g.np) % g.nt;
-    const int is = gam / (g.np * g.nt);
     ConeLocal o;
-    o.gamma = gam;
-    o.r = r;
-    o.ts = fmaf(s, g.s2w, -(float)(2 * is + 1));
-    o.tt = fmaf(th, g.t2w, -(float)(2 * it + 1));
-    float tp = fmaf(ph, g.p2w, -(float)(2 * ip + 1));
+    o.is = (int)(s * g.s_scale);
+    o.it = (int)(th * g.t_scale);
+    o.ip = (int)(ph * g.p_scale);
+    classify_exact(g, vx, vy, vz, r2, o.is, o.it, o.ip);
+    o.r = r2 * rinv;
+    o.ts = fmaf(s, g.s2w, -(float)(2 * o.is + 1));
+    o.tt = fmaf(th, g.t2w, -(float)(2 * o.it + 1));
+    float tp = fmaf(ph, g.p2w, -(float)(2 * o.ip + 1));
     const float span = (float)(2 * g.np);  // 2 pi in local units
     if (tp > (float)g.np) tp -= span;
     if (tp < -(float)g.np) tp += span;
     o.tp = tp;
     return o;
+}
+
+// Classification only (plan-time activation and the FP64 path).
+__device__ __forceinline__ int classify_f32(const LevelGrid& g, float vx, float vy, float vz) {
+    const float r2 = rn_r2(vx, vy, vz);
+    const float s = g.hg * rsqrtf(r2);
+    const float rxy2 = fmaf(vx, vx, vy * vy);
+    const float rxy = rxy2 > 0.0f ? rxy2 * rsqrtf(rxy2) : 0.0f;
+    float ph = fast_atan2(vy, vx);
+    if (ph < 0.0f) ph += 6.28318530717958647692f;
+    int is = (int)(s * g.s_scale), it = (int)(fast_atan2(rxy, vz) * g.t_scale), ip = (int)(ph * g.p_scale);
+    classify_exact(g, vx, vy, vz, r2, is, it, ip);
+    return (is * g.nt + it) * g.np + ip;
 }
 
 // FP64 local coordinates of a physical offset v inside cone gamma of a level grid.
@@ -298,31 +330,75 @@ __device__ __forceinline__ void cheb_T(T t, T* v) {
     for (int n = 2; n < P; ++n) v[n] = t2 * v[n - 1] - v[n - 2];
 }
 
-// Interpolant sum_abc c_abc T_a(ts) T_b(tt) T_c(tp), contracted phi, then theta, then s,
-// with packed FP32x2 FMAs (re and im share the real basis weight).
+// One row (fixed a, b) of the phi contraction: bb = sum_q c_q T_q with packed FP32x2 FMAs.
+__device__ __forceinline__ float2 row5(float2 c0, float2 c1, float2 c2, float2 c3, float2 c4, const float* Tp) {
+    float2 bb = make_float2(c0.x, c0.y);  // T_0 = 1
+    bb = __ffma2_rn(c1, make_float2(Tp[1], Tp[1]), bb);
+    bb = __ffma2_rn(c2, make_float2(Tp[2], Tp[2]), bb);
+    bb = __ffma2_rn(c3, make_float2(Tp[3], Tp[3]), bb);
+    bb = __ffma2_rn(c4, make_float2(Tp[4], Tp[4]), bb);
+    return bb;
+}
+
+// Interpolant sum_abc c_abc T_a(ts) T_b(tt) T_c(tp), contracted phi, then theta, then s, with
+// packed FP32x2 FMAs (re and im share the real basis weight).  For P_phi = 5 two consecutive
+// rows (10 complex = 80 bytes, 16-byte aligned for an even row) are read with five 128-bit
+// loads; the coefficient block of a cone must be 16-byte aligned.
 template <int PS, int PT, int PP>
 __device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float ts, float tt, float tp) {
     float Ts[PS], Tt[PT], Tp[PP];
     cheb_T<PS>(ts, Ts);
     cheb_T<PT>(tt, Tt);
     cheb_T<PP>(tp, Tp);
-    float2 acc = make_float2(0.f, 0.f);
+    if constexpr (PP == 5) {
+        constexpr int R = PS * PT;
+        const float4* c4 = reinterpret_cast<const float4*>(c);
+        float2 aa[PS];
 #pragma unroll
-    for (int a = 0; a < PS; ++a) {
-        float2 aa = make_float2(0.f, 0.f);
+        for (int a = 0; a < PS; ++a) aa[a] = make_float2(0.f, 0.f);
+        // fold row r = a*PT + b into aa[a] with weight T_b(tt) as soon as it is formed
+        auto fold = [&](int rr, float2 row) {
+            const int a = rr / PT, b = rr - (rr / PT) * PT;
+            aa[a] = __ffma2_rn(row, make_float2(Tt[b], Tt[b]), aa[a]);
+        };
 #pragma unroll
-        for (int b = 0; b < PT; ++b) {
-            float2 bb = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int q = 0; q < PP; ++q) {
-                const float2 co = __ldg(c + (a * PT + b) * PP + q);
-                bb = __ffma2_rn(co, make_float2(Tp[q], Tp[q]), bb);
-            }
-            aa = __ffma2_rn(bb, make_float2(Tt[b], Tt[b]), aa);
+        for (int m = 0; m < R / 2; ++m) {
+            const float4 v0 = __ldg(c4 + 5 * m + 0), v1 = __ldg(c4 + 5 * m + 1), v2 = __ldg(c4 + 5 * m + 2);
+            const float4 v3 = __ldg(c4 + 5 * m + 3), v4 = __ldg(c4 + 5 * m + 4);
+            fold(2 * m, row5(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                             make_float2(v1.z, v1.w), make_float2(v2.x, v2.y), Tp));
+            fold(2 * m + 1, row5(make_float2(v2.z, v2.w), make_float2(v3.x, v3.y), make_float2(v3.z, v3.w),
+                                 make_float2(v4.x, v4.y), make_float2(v4.z, v4.w), Tp));
         }
-        acc = __ffma2_rn(aa, make_float2(Ts[a], Ts[a]), acc);
+        if constexpr (R % 2 == 1) {
+            const float4 v0 = __ldg(c4 + 5 * (R / 2) + 0), v1 = __ldg(c4 + 5 * (R / 2) + 1);
+            const float2 v2 = __ldg(c + 10 * (R / 2) + 4);
+            fold(R - 1, row5(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                             make_float2(v1.z, v1.w), v2, Tp));
+        }
+        float2 acc = aa[0];
+#pragma unroll
+        for (int a = 1; a < PS; ++a) acc = __ffma2_rn(aa[a], make_float2(Ts[a], Ts[a]), acc);
+        return acc;
+    } else {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < PS; ++a) {
+            float2 aa = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < PT; ++b) {
+                float2 bb = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const float2 co = __ldg(c + (a * PT + b) * PP + q);
+                    bb = __ffma2_rn(co, make_float2(Tp[q], Tp[q]), bb);
+                }
+                aa = __ffma2_rn(bb, make_float2(Tt[b], Tt[b]), aa);
+            }
+            acc = __ffma2_rn(aa, make_float2(Ts[a], Ts[a]), acc);
+        }
+        return acc;
     }
-    return acc;
 }
 
 template <int PS, int PT, int PP>

@@ -247,8 +247,7 @@ __global__ void k_mark_cousin_points(int64_t N, int D, int d, const int32_t* __r
         const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
         const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
-        const ConeLocal cl = locate_f32(g, vx, vy, vz);
-        mark[(int64_t)B * g.C + cl.gamma] = 1;
+        mark[(int64_t)B * g.C + classify_f32(g, vx, vy, vz)] = 1;
     }
 }
 
@@ -282,8 +281,7 @@ __global__ void k_mark_parent_nodes(int64_t ncp, int P, int Ps, int Pt, int Pp, 
         const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
         const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
         const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
-        const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
-        mark[(int64_t)kb * g.C + cl.gamma] = 1;
+        mark[(int64_t)kb * g.C + classify_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz))] = 1;
     }
 }
 
@@ -316,7 +314,7 @@ void build_grid(Plan& p, int d, const ifgf_options& opt, std::vector<std::vector
     const double eta = std::sqrt(3.0) / 3.0;
     const double Hd = std::ldexp(p.H1, 1 - d);
     int e = 0;
-    while (p.kappa > 0.0 && e < 24 && p.kappa * Hd > 2.0 * M_PI * opt.tau * std::ldexp(1.0, e)) ++e;
+    while (p.kappa > 0.0 && e < 24 && p.kappa * Hd > 2.0 * M_PI * opt.tau * std::ldexp(1.0, e) * (1.0 + std::ldexp(1.0, -10))) ++e;
     const int ns = opt.base_cones[0] << e, nt = opt.base_cones[1] << e, np = opt.base_cones[2] << e;
     LevelGrid& g = p.L[d].g;
     g.ns = ns;
