@@ -400,6 +400,154 @@ k_prop_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __
     }
 }
 
+// Propagation from the node tables of the parent level: the geometry of every (cone index,
+// child octant, node) was computed once at plan time, so an evaluation is a table read, the
+// child cone's slot, the interpolant contraction and the complex ratio.
+template <int PS, int PT, int PP>
+__global__ void __launch_bounds__(kPropThreads, 5)
+k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
+               const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
+               const int32_t* __restrict__ slot, int C, const float4* __restrict__ tab_t,
+               const float2* __restrict__ tab_r, const int32_t* __restrict__ tab_k,
+               const int32_t* __restrict__ tab_list, const int16_t* __restrict__ tab_perm,
+               const float2* __restrict__ cchild,
+               float2* __restrict__ cparent, const float* __restrict__ W, int cstride, int nrhs,
+               int* __restrict__ status) {
+    constexpr int P = PS * PT * PP;
+    constexpr int NC = kPropCones;
+    __shared__ float2 vals[NC][8][P];
+    __shared__ float2 f[NC][P], tmp[NC][P];
+    __shared__ int s_off[NC + 1], s_kb0[NC], s_row[NC][8];
+    __shared__ int s_slot[NC][8][kTabList];
+    const int tid = threadIdx.x;
+    const int r = blockIdx.y;
+    const int64_t pc0 = (int64_t)blockIdx.x * NC;
+    if (tid < NC) {
+        const int c = tid;
+        const int64_t pc = pc0 + c;
+        int nch = 0;
+        if (pc < ncp) {
+            const int jb = pcone_box[pc];
+            const int k0 = pcstart[jb];
+            nch = pcstart[jb + 1] - k0;
+            s_kb0[c] = k0;
+            const int g8 = cone_gidx[pc] * 8;
+            const int4 kj = kp[jb];
+            for (int ch = 0; ch < nch; ++ch) {
+                const int4 kk = kd[k0 + ch];
+                s_row[c][ch] = g8 + ((kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2));
+            }
+        }
+        s_off[c + 1] = nch * P;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_off[0] = 0;
+        for (int c = 0; c < NC; ++c) s_off[c + 1] += s_off[c];
+    }
+    // child-cone slots of every (cone, child) group, once per block; their coefficient blocks
+    // are prefetched into L2 while the slots resolve
+    for (int x = tid; x < NC * 8 * kTabList; x += kPropThreads) {
+        const int k = x % kTabList, g = x / kTabList;
+        const int c = g / 8, ch = g % 8;
+        const int64_t pc = pc0 + c;
+        if (pc >= ncp) continue;
+        const int jb_n = pcstart[pcone_box[pc] + 1] - s_kb0[c];
+        if (ch >= jb_n) continue;
+        const int row = s_row[c][ch];
+        if (k >= __ldg(&tab_k[row])) continue;
+        const int sl = __ldg(&slot[(int64_t)(s_kb0[c] + ch) * C + __ldg(&tab_list[(int64_t)row * kTabList + k])]);
+        s_slot[c][ch][k] = sl;
+        if (sl >= 0) {
+            const char* blk = reinterpret_cast<const char*>(cchild + ((int64_t)sl * nrhs + r) * cstride);
+#pragma unroll
+            for (int off = 0; off < P * 8; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + off));
+        }
+    }
+    __syncthreads();
+    const int total = s_off[NC];
+    for (int item = tid; item < total; item += kPropThreads) {
+        int c = 0;
+#pragma unroll
+        for (int k = 1; k < NC; ++k) c += item >= s_off[k];
+        const int rem = item - s_off[c];
+        const int ch = rem / P, j = rem - ch * P;
+        const int64_t rowP = (int64_t)s_row[c][ch] * P;
+        const int n = __ldg(&tab_perm[rowP + j]);  // nodes ordered by child cone: warps share blocks
+        const int64_t e = rowP + n;
+        const float4 t4 = __ldg(&tab_t[e]);
+        const float2 ratio = __ldg(&tab_r[e]);
+        const int kl = __float_as_int(t4.w);
+        const int s = (unsigned)kl < (unsigned)kTabList ? s_slot[c][ch][kl] : -1;
+        float2 t = make_float2(0.f, 0.f);
+        if (s < 0) {
+            set_status(status, IFGF_ERR_INTERNAL);
+        } else {
+            const float2 F = interp_f32<PS, PT, PP>(cchild + ((int64_t)s * nrhs + r) * cstride, t4.x, t4.y, t4.z);
+            t = cmul(F, ratio);
+        }
+        vals[c][ch][n] = t;
+    }
+    __syncthreads();
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int nch = (s_off[c + 1] - s_off[c]) / P;
+        float2 a = make_float2(0.f, 0.f);
+        for (int ch = 0; ch < nch; ++ch) {
+            a.x += vals[c][ch][n].x;
+            a.y += vals[c][ch][n].y;
+        }
+        f[c][n] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 acc = make_float2(0.f, 0.f);
+        const float2* rw = &f[c][(qa * PT + qb) * PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const float w = Wp[qc * PP + k];
+            acc.x = fmaf(w, rw[k].x, acc.x);
+            acc.y = fmaf(w, rw[k].y, acc.y);
+        }
+        tmp[c][n] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < PT; ++j) {
+            const float w = Wt[qb * PT + j];
+            const float2 v = tmp[c][(qa * PT + j) * PP + qc];
+            acc.x = fmaf(w, v.x, acc.x);
+            acc.y = fmaf(w, v.y, acc.y);
+        }
+        f[c][n] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < NC * P; x += kPropThreads) {
+        const int c = x / P, n = x - (x / P) * P;
+        const int64_t pc = pc0 + c;
+        if (pc >= ncp) continue;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const float w = Ws[qa * PS + i];
+            const float2 v = f[c][(i * PT + qb) * PP + qc];
+            acc.x = fmaf(w, v.x, acc.x);
+            acc.y = fmaf(w, v.y, acc.y);
+        }
+        cparent[(pc * nrhs + r) * cstride + n] = acc;
+    }
+}
+
 template <int PS, int PT, int PP>
 __global__ void k_prop_f64(const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
                            const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
@@ -605,7 +753,13 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                 }
             if (d == 3) break;
             Level& Lp = p.L[d - 1];
-            if (Lp.nc > 0)
+            if (Lp.nc > 0 && Lp.n_gam > 0) {
+                TimedScope ts_(TK_PROP, s);
+                IFGF_LAUNCH((k_prop_tab_f32<PS, PT, PP>), dim3((unsigned)((Lp.nc + kPropCones - 1) / kPropCones), nrhs),
+                            kPropThreads, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, L.slot, L.g.C,
+                            Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, (const float2*)p.coef[cur],
+                            (float2*)p.coef[1 - cur], p.Wf, p.cstride, nrhs, p.d_status);
+            } else if (Lp.nc > 0)
                 {
                     TimedScope ts_(TK_PROP, s);
                     IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((Lp.nc + kPropCones - 1) / kPropCones), nrhs),

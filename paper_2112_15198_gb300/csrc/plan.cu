@@ -285,6 +285,130 @@ __global__ void k_mark_parent_nodes(int64_t ncp, int P, int Ps, int Pt, int Pp, 
     }
 }
 
+// ---- node tables (translation invariance of the propagation geometry) ------------------
+__global__ void k_flag_gamma(const int32_t* __restrict__ cone_gam, int64_t nc, int32_t* __restrict__ flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) flags[cone_gam[i]] = 1;
+}
+
+__global__ void k_gamma_rows(const int32_t* __restrict__ flags, const int32_t* __restrict__ pos, int C,
+                             int32_t* __restrict__ gam_list) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < C && flags[i]) gam_list[pos[i]] = i;
+}
+
+__global__ void k_cone_rows(const int32_t* __restrict__ cone_gam, int64_t nc, const int32_t* __restrict__ pos,
+                            int32_t* __restrict__ cone_gidx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) cone_gidx[i] = pos[cone_gam[i]];
+}
+
+// Entry (g*8 + o)*P + n: node n of cone index gam_list[g] of the parent grid, seen from the
+// child centre at octant o (bit 0: +x half, bit 1: +y, bit 2: +z); offsets in child grid units.
+__global__ void k_node_tables(int64_t total, const int32_t* __restrict__ gam_list, int Ps, int Pt, int Pp, int sh,
+                              LevelGrid gp, LevelGrid g, float ku, float4* __restrict__ tab_t,
+                              float2* __restrict__ tab_r) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int P = Ps * Pt * Pp;
+    const int n = (int)(e % P);
+    const int o = (int)((e / P) % 8);
+    const int gam = gam_list[e / (8 * (int64_t)P)];
+    const int ip = gam % gp.np, it = (gam / gp.np) % gp.nt, is = gam / (gp.np * gp.nt);
+    const int qc = n % Pp, qb = (n / Pp) % Pt, qa = n / (Pp * Pt);
+    const float rho = gp.rho[is * Ps + qa];
+    const float st = gp.stn[it * Pt + qb], ct = gp.ctn[it * Pt + qb];
+    const float cp = gp.cpn[ip * Pp + qc], sp = gp.spn[ip * Pp + qc];
+    const float qx = __fmul_rn(rho, __fmul_rn(st, cp)), qy = __fmul_rn(rho, __fmul_rn(st, sp));
+    const float qz = __fmul_rn(rho, ct);
+    const float ox = (float)((2 * (o & 1) - 1) << sh);
+    const float oy = (float)((2 * ((o >> 1) & 1) - 1) << sh);
+    const float oz = (float)((2 * ((o >> 2) & 1) - 1) << sh);
+    const ConeLocal cl = locate_f32(g, __fsub_rn(qx, ox), __fsub_rn(qy, oy), __fsub_rn(qz, oz));
+    const float rj = sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz)));
+    const float oo = 3.0f * (float)(1 << sh) * (float)(1 << sh);
+    const float qo = fmaf(qx, ox, fmaf(qy, oy, qz * oz));
+    // G(x,x_k)/G(x,x_j) = (r_j/r_k) exp(i kappa (r_k - r_j)), r_k - r_j = (|o|^2 - 2 q.o)/(r_k + r_j)
+    const float dr = fmaf(-2.f, qo, oo) / (cl.r + rj);
+    const float2 ex = cis_f32(ku * dr);
+    const float w = rj / cl.r;
+    tab_t[e] = make_float4(cl.ts, cl.tt, cl.tp, __int_as_float(cl.gamma(g)));
+    tab_r[e] = make_float2(ex.x * w, ex.y * w);
+}
+
+// Distinct child cones of each table row (gamma, octant): the list, and each node's position in
+// it (replacing the cone index in tab_t.w).  Rows are built from the 75-node classification, so
+// K <= 75; the build rejects K > kTabList (the plan then computes that level's geometry).
+__global__ void k_node_lists(int P, float4* __restrict__ tab_t, int32_t* __restrict__ tab_k,
+                             int32_t* __restrict__ tab_list, int16_t* __restrict__ tab_perm,
+                             int* __restrict__ overflow) {
+    __shared__ int alpha[128];  // child cone of each node
+    __shared__ int first[128];  // 1 if the node is the first with its child cone
+    __shared__ int idx[128];    // list position, defined where first[] is set
+    __shared__ int kpos[128];   // list position of every node
+    const int64_t row = blockIdx.x;
+    const int n = threadIdx.x;
+    if (n < P) alpha[n] = __float_as_int(tab_t[row * P + n].w);
+    __syncthreads();
+    if (n < P) {
+        int f = 1;
+        for (int m = 0; m < n; ++m)
+            if (alpha[m] == alpha[n]) f = 0;
+        first[n] = f;
+    }
+    __syncthreads();
+    if (n == 0) {
+        int K = 0;
+        for (int m = 0; m < P; ++m) {
+            if (first[m]) {
+                if (K < kTabList) tab_list[row * kTabList + K] = alpha[m];
+                idx[m] = K++;
+            }
+        }
+        tab_k[row] = K;
+        if (K > kTabList) atomicExch(overflow, 1);
+    }
+    __syncthreads();
+    if (n < P) {
+        int k = 0;
+        for (int m = 0; m <= n; ++m)
+            if (first[m] && alpha[m] == alpha[n]) k = idx[m];
+        kpos[n] = k;
+    }
+    __syncthreads();
+    if (n < P) {
+        const int k = kpos[n];
+        float4 t = tab_t[row * P + n];
+        t.w = __int_as_float(k);
+        tab_t[row * P + n] = t;
+        // stable position of node n among the row's nodes ordered by child cone
+        int pos = 0;
+        for (int m = 0; m < P; ++m) pos += (kpos[m] < k) || (kpos[m] == k && m < n);
+        tab_perm[row * P + pos] = (int16_t)n;
+    }
+}
+
+// Activation from the node tables: every node of every relevant parent cone marks the child
+// cone its table entry names (the same exact classification, computed once per gamma).
+__global__ void k_mark_parent_nodes_tab(int64_t ncp, const int32_t* __restrict__ pcone_box,
+                                        const int32_t* __restrict__ cone_gidx, const int4* __restrict__ kp,
+                                        const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
+                                        const int32_t* __restrict__ tab_k, const int32_t* __restrict__ tab_list,
+                                        int C, int32_t* __restrict__ mark) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncp * kTabList) return;
+    const int64_t pc = t / kTabList;
+    const int k = (int)(t - pc * kTabList);
+    const int jb = pcone_box[pc];
+    const int64_t row = (int64_t)cone_gidx[pc] * 8;
+    const int4 kj = kp[jb];
+    for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
+        const int4 kk = kd[kb];
+        const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
+        if (k < tab_k[row + o]) mark[(int64_t)kb * C + tab_list[(row + o) * kTabList + k]] = 1;
+    }
+}
+
 __global__ void k_finalize_cones(int32_t* __restrict__ slot, const int32_t* __restrict__ pos, int64_t total, int C,
                                  int32_t* __restrict__ cone_box, int32_t* __restrict__ cone_gam) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,6 +537,57 @@ __global__ void k_dup_check(const double* __restrict__ Xs, int64_t N, const uint
 }
 
 }  // namespace
+
+// Node tables of level dp (for its children at dp+1), when the cone indices are shared by
+// enough boxes and the tables stay small; otherwise the kernels compute the geometry.
+void build_node_tables(Plan& p, int dp) {
+    Level& Lp = p.L[dp];
+    Level& L = p.L[dp + 1];
+    Lp.n_gam = 0;
+    if (Lp.nc == 0) return;
+    const int C = Lp.g.C;
+    int32_t* flags = dalloc<int32_t>(p, C);
+    int32_t* pos = dalloc<int32_t>(p, C);
+    IFGF_CUDA(cudaMemsetAsync(flags, 0, sizeof(int32_t) * C, p.stream));
+    IFGF_LAUNCH(k_flag_gamma, grid_for(Lp.nc, kThreads), kThreads, 0, p.stream, Lp.cone_gam, Lp.nc, flags);
+    exclusive_scan_i32(p, flags, pos, C);
+    const int32_t n_gam = read_one(p, pos + (C - 1)) + read_one(p, flags + (C - 1));
+    const int64_t entries = (int64_t)n_gam * 8 * p.P;
+    const double sharing = (double)Lp.nc / std::max(1, n_gam);
+    if (sharing >= 4.0 && entries * 24 <= ((int64_t)1 << 30)) {
+        Lp.n_gam = n_gam;
+        Lp.gam_list = dalloc<int32_t>(p, n_gam);
+        Lp.cone_gidx = dalloc<int32_t>(p, Lp.nc);
+        Lp.tab_t = dalloc<float4>(p, entries);
+        Lp.tab_r = dalloc<float2>(p, entries);
+        IFGF_LAUNCH(k_gamma_rows, grid_for(C, kThreads), kThreads, 0, p.stream, flags, pos, C, Lp.gam_list);
+        IFGF_LAUNCH(k_cone_rows, grid_for(Lp.nc, kThreads), kThreads, 0, p.stream, Lp.cone_gam, Lp.nc, pos,
+                    Lp.cone_gidx);
+        IFGF_LAUNCH(k_node_tables, grid_for(entries, kThreads), kThreads, 0, p.stream, entries, Lp.gam_list, p.Ps, p.Pt,
+                    p.Pp, p.D - (dp + 1), Lp.g, L.g, (float)(p.kappa * p.u), Lp.tab_t, Lp.tab_r);
+        Lp.tab_k = dalloc<int32_t>(p, (size_t)n_gam * 8);
+        Lp.tab_list = dalloc<int32_t>(p, (size_t)n_gam * 8 * kTabList);
+        Lp.tab_perm = dalloc<int16_t>(p, (size_t)entries);
+        int* ovf = dalloc<int>(p, 1);
+        IFGF_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), p.stream));
+        IFGF_LAUNCH(k_node_lists, (unsigned)(n_gam * 8), 128, 0, p.stream, p.P, Lp.tab_t, Lp.tab_k, Lp.tab_list,
+                    Lp.tab_perm, ovf);
+        const int overflow = read_one(p, ovf);
+        dfree_ptr(p, ovf);
+        if (overflow) {  // some row has more distinct child cones than a list holds: no tables
+            dfree_ptr(p, Lp.gam_list);
+            dfree_ptr(p, Lp.cone_gidx);
+            dfree_ptr(p, Lp.tab_t);
+            dfree_ptr(p, Lp.tab_r);
+            dfree_ptr(p, Lp.tab_k);
+            dfree_ptr(p, Lp.tab_list);
+            dfree_ptr(p, Lp.tab_perm);
+            Lp.n_gam = 0;
+        }
+    }
+    dfree_ptr(p, flags);
+    dfree_ptr(p, pos);
+}
 
 void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
     const int64_t N = p.N;
@@ -549,7 +724,10 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
                     p.L[D].k, L.k, L.ncs, L.cs, p.off, L.g, L.slot);
         if (d > 3) {
             Level& Lp = p.L[d - 1];
-            if (Lp.nc > 0)
+            if (Lp.nc > 0 && Lp.n_gam > 0)
+                IFGF_LAUNCH(k_mark_parent_nodes_tab, grid_for(Lp.nc * kTabList, kThreads), kThreads, 0, s, Lp.nc,
+                            Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, Lp.tab_k, Lp.tab_list, L.g.C, L.slot);
+            else if (Lp.nc > 0)
                 IFGF_LAUNCH(k_mark_parent_nodes, grid_for(Lp.nc * p.P, kThreads), kThreads, 0, s, Lp.nc, p.P, p.Ps,
                             p.Pt, p.Pp, D, d, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, Lp.g, L.g, L.slot);
         }
@@ -563,6 +741,7 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
         IFGF_LAUNCH(k_finalize_cones, grid_for(total, kThreads), kThreads, 0, s, L.slot, cpos, total, L.g.C,
                     L.cone_box, L.cone_gam);
         dfree_ptr(p, cpos);
+        if (d < D && p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5) build_node_tables(p, d);
     }
 }
 
