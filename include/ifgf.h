@@ -30,6 +30,7 @@ extern "C" {
 #endif
 
 typedef struct ifgf_plan_s* ifgf_plan;
+typedef struct ifgf_batch_s* ifgf_batch;
 
 typedef enum {
     IFGF_OK = 0,
@@ -120,6 +121,24 @@ ifgf_status ifgf_apply_ex(ifgf_plan plan, const void* densities, int32_t nrhs, v
 ifgf_status ifgf_plan_destroy(ifgf_plan plan);
 
 /*
+ * Batched evaluation of many independent problems (each its own plan, e.g. bodies of different
+ * sizes) as one launch sequence: the operator of Eq. (1) is applied to every plan in order.
+ * The first ifgf_batch_apply with a given set of buffers captures the applies into a CUDA graph
+ * on a private stream; later calls with the same buffers replay that graph with one launch on
+ * `stream` (other buffers trigger a new capture).  Plans must live on one device, must outlive
+ * the batch, and must not be applied elsewhere while the batch runs (they own their scratch).
+ *
+ *   plans  n plan handles (not owned).
+ *   dens   n device pointers, plan i's densities as in ifgf_apply.
+ *   nrhs   n counts, 1 <= nrhs[i] <= that plan's max_nrhs.
+ *   outs   n device pointers, plan i's outputs.
+ */
+ifgf_status ifgf_batch_create(const ifgf_plan* plans, int32_t n, ifgf_batch* out_batch);
+ifgf_status ifgf_batch_apply(ifgf_batch batch, const void* const* dens, const int32_t* nrhs, void* const* outs,
+                             void* stream);
+ifgf_status ifgf_batch_destroy(ifgf_batch batch);
+
+/*
  * Introspection (synchronous).  Copies the requested array into host_buf as int64 values
  * when host_buf != NULL and *inout_count is large enough; always stores the element count
  * in *inout_count.  `level` selects the octree level where the item is per level.
@@ -140,7 +159,8 @@ enum {
     IFGF_Q_INFO = 12,       /* [44] N, D, n_1..n_21, c_1..c_21 */
     IFGF_Q_WORK = 13,       /* [4] near pairs, leaf pairs, level-d interpolations, level-d propagations */
     IFGF_Q_STATUS = 14,     /* [1] sticky device status (ifgf_status) */
-    IFGF_Q_CHILD_START = 15 /* [n_d + 1] first child box in level d+1 */
+    IFGF_Q_CHILD_START = 15, /* [n_d + 1] first child box in level d+1 */
+    IFGF_Q_BOX_COORDS = 16   /* [n_d * 3] integer box coordinates (k_x, k_y, k_z) */
 };
 ifgf_status ifgf_plan_query(ifgf_plan plan, int32_t what, int32_t level, int64_t* host_buf, int64_t* inout_count);
 

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["IFGFError", "Plan", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q",
+__all__ = ["IFGFError", "Plan", "Batch", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q",
            "PREC_FP64", "PREC_MIXED"]
 
 PREC_FP64 = 0
@@ -29,7 +29,7 @@ class Q:
 
     PERM, KEYS, BOX_KEYS, BOX_START, BOX_PARENT = 0, 1, 2, 3, 4
     NBR_COUNT, NBR_LIST, COUS_COUNT, COUS_LIST = 5, 6, 7, 8
-    CONE_BOX, CONE_GAMMA, GRID, INFO, WORK, STATUS, CHILD_START = 9, 10, 11, 12, 13, 14, 15
+    CONE_BOX, CONE_GAMMA, GRID, INFO, WORK, STATUS, CHILD_START, BOX_COORDS = 9, 10, 11, 12, 13, 14, 15, 16
 
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED"}
@@ -91,6 +91,12 @@ def load(build: bool = True):
         lib.ifgf_last_error.restype = ctypes.c_char_p
         lib.ifgf_launch_count.argtypes = []
         lib.ifgf_launch_count.restype = i64
+        lib.ifgf_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+        lib.ifgf_batch_create.restype = ctypes.c_int
+        lib.ifgf_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp), vp]
+        lib.ifgf_batch_apply.restype = ctypes.c_int
+        lib.ifgf_batch_destroy.argtypes = [vp]
+        lib.ifgf_batch_destroy.restype = ctypes.c_int
         lib.ifgf_timing_enable.argtypes = [i32]
         lib.ifgf_timing_enable.restype = None
         lib.ifgf_timing_collect.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(i64)]
@@ -229,3 +235,38 @@ class Plan:
 
     def __exit__(self, *exc):
         self.destroy()
+
+
+class Batch:
+    """Many plans applied as one CUDA-graph launch sequence (ifgf_batch_*)."""
+
+    def __init__(self, plans):
+        lib = load()
+        self._lib = lib
+        self._plans = list(plans)  # keep the plans alive
+        arr = (ctypes.c_void_p * len(self._plans))(*(p._h.value for p in self._plans))
+        h = ctypes.c_void_p()
+        _check(lib.ifgf_batch_create(arr, len(self._plans), ctypes.byref(h)))
+        self._h = h
+
+    def apply(self, dens_list, out_list, nrhs_list=None, stream=None):
+        n = len(self._plans)
+        if nrhs_list is None:
+            nrhs_list = [1 if len(d.shape) == 1 else int(d.shape[0]) for d in dens_list]
+        d = (ctypes.c_void_p * n)(*(_ptr(x) for x in dens_list))
+        o = (ctypes.c_void_p * n)(*(_ptr(x) for x in out_list))
+        r = (ctypes.c_int32 * n)(*(int(x) for x in nrhs_list))
+        _check(self._lib.ifgf_batch_apply(self._h, d, r, o, _stream(stream)))
+        return out_list
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _check(self._lib.ifgf_batch_destroy(h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -56,6 +56,11 @@ TimedScope::TimedScope(int k, cudaStream_t s) : kind(k), stream(s) {
     TimingState& t = timing();
     std::lock_guard<std::mutex> lk(t.mu);
     if (!t.on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;  // no timing events inside a graph capture
+    }
     start = t.get();
     cudaEventRecord(start, s);
 }
@@ -101,10 +106,17 @@ ifgf_status guard(const std::function<void()>& f) {
     }
 }
 }  // namespace
+
+ifgf_status guard_call(const std::function<void()>& f) { return guard(f); }
+
 }  // namespace ifgf
 
 // The opaque handle of the C ABI is the plan itself.
 struct ifgf_plan_s : public ifgf::Plan {};
+
+namespace ifgf {
+Plan* plan_of(ifgf_plan p) { return p; }
+}  // namespace ifgf
 
 using namespace ifgf;
 
@@ -300,6 +312,13 @@ ifgf_status ifgf_plan_query(ifgf_plan plan, int32_t what, int32_t level, int64_t
                 need(lev_ok);
                 auto h = get32(L.parent, L.n);
                 res.assign(h.begin(), h.end());
+                break;
+            }
+            case IFGF_Q_BOX_COORDS: {
+                need(lev_ok);
+                std::vector<int4> h((size_t)L.n);
+                IFGF_CUDA(cudaMemcpy(h.data(), L.k, sizeof(int4) * L.n, cudaMemcpyDeviceToHost));
+                for (const int4& v : h) res.insert(res.end(), {v.x, v.y, v.z});
                 break;
             }
             case IFGF_Q_CHILD_START: {

@@ -177,32 +177,33 @@ __device__ __forceinline__ int find_box(const uint64_t* __restrict__ keys, int n
     return -1;
 }
 
-// Neighbours N B (Eq. (2)): relevant boxes with ||j - k||_inf <= 1, ascending.
+// Neighbours N B (Eq. (2)): relevant boxes with ||j - k||_inf <= 1, ascending.  The 27
+// candidate lookups fill a register array (fully unrolled), then an ascending selection pass
+// writes the list.
 __global__ void k_neighbours(const uint64_t* __restrict__ keys, const int4* __restrict__ bk, int n, int d,
                              int32_t* __restrict__ nnb, int32_t* __restrict__ nb) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n) return;
     const int4 k = bk[b];
     const int side = 1 << (d - 1);
-    int list[kMaxNbr];
-    int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int x = k.x + dx, y = k.y + dy, z = k.z + dz;
-                if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
-                const int q = find_box(keys, n, morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
-                if (q >= 0) {
-                    int j = cnt++;
-                    while (j > 0 && list[j - 1] > q) {
-                        list[j] = list[j - 1];
-                        --j;
-                    }
-                    list[j] = q;
-                }
-            }
+    int found[kMaxNbr];
+#pragma unroll
+    for (int c = 0; c < kMaxNbr; ++c) {
+        const int x = k.x + (c % 3) - 1, y = k.y + ((c / 3) % 3) - 1, z = k.z + (c / 9) - 1;
+        const bool in = x >= 0 && y >= 0 && z >= 0 && x < side && y < side && z < side;
+        found[c] = in ? find_box(keys, n, morton3((uint32_t)x, (uint32_t)y, (uint32_t)z)) : -1;
+    }
+    int cnt = 0, last = -1;
+    for (int t = 0; t < kMaxNbr; ++t) {
+        int best = 0x7fffffff;
+#pragma unroll
+        for (int c = 0; c < kMaxNbr; ++c)
+            if (found[c] > last && found[c] < best) best = found[c];
+        if (best == 0x7fffffff) break;
+        nb[(int64_t)b * kMaxNbr + cnt++] = best;
+        last = best;
+    }
     nnb[b] = cnt;
-    for (int t = 0; t < cnt; ++t) nb[(int64_t)b * kMaxNbr + t] = list[t];
 }
 
 // Cousins M B (Eq. (2)): children of the parent's neighbours that are not neighbours.  The

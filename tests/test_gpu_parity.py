@@ -46,6 +46,14 @@ def assert_same_tree(gp, op):
     np.testing.assert_array_equal(gp.query(Qg.PERM), op.get(Qo.Q_PERM))
     np.testing.assert_array_equal(gp.query(Qg.KEYS), op.get(Qo.Q_KEYS))
     for d in range(1, gp.D + 1):
+        keys = gp.query(Qg.BOX_KEYS, d)
+        coords = gp.query(Qg.BOX_COORDS, d).reshape(-1, 3)
+        for b in range(0, len(keys), max(1, len(keys) // 64)):  # coordinates decode the keys
+            k = [0, 0, 0]
+            for bit in range(21):
+                for ax in range(3):
+                    k[ax] |= ((int(keys[b]) >> (3 * bit + ax)) & 1) << bit
+            assert tuple(coords[b]) == tuple(k)
         for qg, qo in ((Qg.BOX_KEYS, Qo.Q_BOX_KEYS), (Qg.BOX_START, Qo.Q_BOX_START), (Qg.BOX_PARENT, Qo.Q_BOX_PARENT)):
             np.testing.assert_array_equal(gp.query(qg, d), op.get(qo, d), err_msg=f"item {qg} level {d}")
         if d < gp.D:
@@ -72,6 +80,9 @@ CASES = {
                                  np.zeros(3000)]), 2 * math.pi * 4, {}),
     "deep": lambda: (W.fibonacci_sphere(3000), 2 * math.pi * 2, {"levels": 7}),
     "laplace": lambda: (W.fibonacci_sphere(12000), 0.0, {}),
+    # (a, a, a/2) spheroid of the uneven batch: its leaf neighbour lists once came out truncated
+    "batch_spheroid": lambda: (W.batch_problems(count=6, seed=17)[1].points(),
+                               W.batch_problems(count=6, seed=17)[1].kappa, {}),
 }
 
 
@@ -84,7 +95,7 @@ def test_tree_and_cones_bit_exact(case):
 
 
 @pytest.mark.parametrize("case", ["sphere4", "cloud_ragged", "spheroid", "two_points", "one_leaf_D3", "planar",
-                                  "deep", "laplace"])
+                                  "deep", "laplace", "batch_spheroid"])
 def test_fp64_matches_cpu_ifgf(case):
     pts, kappa, kw = CASES[case]()
     n = pts.shape[1]
@@ -97,7 +108,7 @@ def test_fp64_matches_cpu_ifgf(case):
 
 
 @pytest.mark.parametrize("case", ["sphere4", "cloud_ragged", "spheroid", "two_points", "one_leaf_D3", "planar",
-                                  "deep", "laplace"])
+                                  "deep", "laplace", "batch_spheroid"])
 def test_mixed_matches_cpu_ifgf(case):
     pts, kappa, kw = CASES[case]()
     n = pts.shape[1]
