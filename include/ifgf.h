@@ -57,6 +57,9 @@ typedef enum {
  *   leaf_target when levels == 0, D is the smallest level >= 3 whose mean relevant-leaf
  *               occupancy N / n_D is at most leaf_target.
  *   max_nrhs    largest nrhs that ifgf_apply will accept (buffers are sized for it).
+ *   rhs_block   the coefficient buffers hold this many densities; ifgf_apply sweeps the levels
+ *               once per block of densities (0: the largest block, up to max_nrhs, whose two
+ *               coefficient buffers fit in half the free device memory at plan time).
  */
 typedef struct {
     int32_t struct_size;   /* sizeof(ifgf_options) */
@@ -64,7 +67,7 @@ typedef struct {
     int32_t base_cones[3];
     int32_t leaf_target;
     int32_t max_nrhs;
-    int32_t reserved;
+    int32_t rhs_block;     /* densities per level sweep; 0 = as many as fit half the free memory */
     double tau;
 } ifgf_options;
 

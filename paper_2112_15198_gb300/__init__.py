@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
         ("base_cones", ctypes.c_int32 * 3),
         ("leaf_target", ctypes.c_int32),
         ("max_nrhs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("rhs_block", ctypes.c_int32),
         ("tau", ctypes.c_double),
     ]
 
@@ -154,7 +154,7 @@ class Plan:
 
     def __init__(self, points, kappa: float, orders=(3, 5, 5), levels: int = 0, precision: str = "mixed",
                  base_cones=(2, 4, 8), tau: float = 0.5, leaf_target: int = 64, max_nrhs: int = 1, stream=None,
-                 n: int | None = None):
+                 n: int | None = None, rhs_block: int = 0):
         lib = load()
         self._lib = lib
         opt = Options()
@@ -164,6 +164,7 @@ class Plan:
         opt.tau = float(tau)
         opt.leaf_target = int(leaf_target)
         opt.max_nrhs = int(max_nrhs)
+        opt.rhs_block = int(rhs_block)
         if n is None:
             shape = tuple(points.shape)
             if len(shape) != 2 or shape[0] != 3:

@@ -1,4 +1,5 @@
 // extern "C" boundary of the library: argument checks, plan lifetime, queries, errors.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -161,6 +162,7 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
         why = "base_cones must be >= (1, 1, 4) with an even azimuthal count";
     else if (opt.leaf_target < 1) why = "leaf_target must be >= 1";
     else if (opt.max_nrhs < 1 || opt.max_nrhs > 65535) why = "max_nrhs out of range";
+    else if (opt.rhs_block < 0) why = "rhs_block must be >= 0";
     else if (!(opt.tau > 0.0) || !std::isfinite(opt.tau)) why = "tau must be finite and > 0";
     else if (!((Ps == 3 && Pt == 5 && Pp == 5) || (Ps == 5 && Pt == 7 && Pp == 7)))
         why = "orders must be (3,5,5) or (5,7,7) in this build";
@@ -205,7 +207,19 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
         int64_t cmax = 1;
         for (int d = 3; d <= p->D; ++d) cmax = std::max<int64_t>(cmax, p->L[d].nc);
         p->coef_cap = cmax;
-        const size_t cbytes = (size_t)cmax * p->max_nrhs * p->cstride * csz;
+        // Coefficient buffers for a block of densities that fits half of the free device memory
+        // (a multiple of 4 when blocked); ifgf_apply sweeps the levels once per block.
+        {
+            size_t free_b = 0, total_b = 0;
+            IFGF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            const size_t per_rhs = 2 * (size_t)cmax * p->cstride * csz;
+            const size_t fit = std::max<size_t>(1, (free_b / 2) / std::max<size_t>(per_rhs, 1));
+            int blk = (int)std::min<size_t>((size_t)p->max_nrhs, fit);
+            if (blk < p->max_nrhs && blk >= 8) blk &= ~3;
+            if (opt.rhs_block > 0) blk = std::min(opt.rhs_block, p->max_nrhs);
+            p->rhs_block = std::max(1, blk);
+        }
+        const size_t cbytes = (size_t)cmax * p->rhs_block * p->cstride * csz;
         p->coef[0] = dalloc<char>(*p, cbytes);
         p->coef[1] = dalloc<char>(*p, cbytes);
         p->a_s = dalloc<char>(*p, (size_t)N * p->max_nrhs * csz);

@@ -8,6 +8,7 @@
 //          the analytic factor and the propagation ratio are written in cancellation-free
 //          forms whose phases stay below kappa h_d.
 //   fp64   every value in FP64 on physical coordinates.
+#include <algorithm>
 #include <cmath>
 
 #include "ifgf_internal.cuh"
@@ -703,7 +704,490 @@ __global__ void k_interp_f64(int64_t N, int sh, const int32_t* __restrict__ pbox
     *dst = make_double2(prev.x + acc.x, prev.y + acc.y);
 }
 
+// ---- many densities: tensor-core contractions (3xTF32) -----------------------------------------
+// With nrhs densities the interpolant of a cone at a set of points is the dense product
+// [points x P basis] * [P coefficients x (nrhs x re/im)]: one warp takes 16 points, and for each
+// distinct cone among them an m16n8k8 TF32 MMA block (3xTF32 for FP32 accuracy) over 4*NT
+// densities; the complex factor of each point is applied to its row in the epilogue.
+constexpr int kMmaMinRhs = 4;    // densities from which the tensor-core kernels are used
+constexpr int kChunk = 16;       // points per warp in the tensor-core kernels
+
+// Distinct-cone loop of one warp: rows (r0, r1) of this thread carry cones a0, a1 (or are done);
+// the warp visits each distinct cone once, calling body(alpha, mask0, mask1).
+template <class Body>
+__device__ __forceinline__ void for_each_cone(int a0, int a1, bool pend0, bool pend1, Body&& body) {
+    for (int guard = 0; guard < 2 * kChunk; ++guard) {
+        const unsigned pend = __ballot_sync(0xffffffffu, pend0 || pend1);
+        if (!pend) break;
+        const int src = __ffs(pend) - 1;
+        const int alpha = __shfl_sync(0xffffffffu, pend0 ? a0 : a1, src);
+        const bool m0 = pend0 && a0 == alpha, m1 = pend1 && a1 == alpha;
+        body(alpha, m0, m1);
+        pend0 = pend0 && !m0;
+        pend1 = pend1 && !m1;
+    }
+}
+
+template <int PS, int PT, int PP, int NT>
+__global__ void __launch_bounds__(32 * ((PS * PT * PP + kChunk - 1) / kChunk))
+k_prop_mma(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
+           const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
+           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
+           const float2* __restrict__ cchild, float2* __restrict__ cparent, int sh, float ku,
+           const float* __restrict__ W, int cstride, int nrhs, int* __restrict__ status) {
+    constexpr int P = PS * PT * PP;
+    constexpr int NR = 4 * NT;
+    constexpr int NTHR = 32 * ((P + kChunk - 1) / kChunk);
+    __shared__ float2 f[NR][P], tmp[NR][P];
+    const int64_t pc = blockIdx.x;
+    const int rhs0 = blockIdx.y * NR;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const int n0 = warp * kChunk + gq, n1 = n0 + 8;
+    const bool v0 = n0 < P, v1 = n1 < P;
+    const int jb = pcone_box[pc], gam = pcone_gam[pc];
+    const int4 kj = kp[jb];
+    auto node = [&](int n) -> float4 {
+        const int ip = gam % gp.np, it = (gam / gp.np) % gp.nt, is = gam / (gp.np * gp.nt);
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        const float rho = gp.rho[is * PS + qa];
+        const float st = gp.stn[it * PT + qb], ct = gp.ctn[it * PT + qb];
+        const float cp = gp.cpn[ip * PP + qc], sp = gp.spn[ip * PP + qc];
+        const float qx = __fmul_rn(rho, __fmul_rn(st, cp)), qy = __fmul_rn(rho, __fmul_rn(st, sp));
+        const float qz = __fmul_rn(rho, ct);
+        return make_float4(qx, qy, qz, sqrtf(fmaf(qx, qx, fmaf(qy, qy, qz * qz))));
+    };
+    const float4 q0 = v0 ? node(n0) : make_float4(0.f, 0.f, 1.f, 1.f);
+    const float4 q1 = v1 ? node(n1) : make_float4(0.f, 0.f, 1.f, 1.f);
+    const float oo = 3.0f * (float)(1 << sh) * (float)(1 << sh);
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
+        const int4 kk = kd[kb];
+        const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
+        const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
+        const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
+        const ConeLocal c0 = locate_f32(g, __fsub_rn(q0.x, ox), __fsub_rn(q0.y, oy), __fsub_rn(q0.z, oz));
+        const ConeLocal c1 = locate_f32(g, __fsub_rn(q1.x, ox), __fsub_rn(q1.y, oy), __fsub_rn(q1.z, oz));
+        auto ratio = [&](const float4& q, const ConeLocal& cl) -> float2 {
+            const float qo = fmaf(q.x, ox, fmaf(q.y, oy, q.z * oz));
+            const float dr = __fdividef(fmaf(-2.f, qo, oo), cl.r + q.w);
+            const float2 e = cis_f32(ku * dr);
+            const float w = __fdividef(q.w, cl.r);
+            return make_float2(e.x * w, e.y * w);
+        };
+        const float2 rt0 = ratio(q0, c0), rt1 = ratio(q1, c1);
+        float Ts0[PS], Tt0[PT], Tp0[PP], Ts1[PS], Tt1[PT], Tp1[PP];
+        cheb_T<PS>(c0.ts, Ts0);
+        cheb_T<PT>(c0.tt, Tt0);
+        cheb_T<PP>(c0.tp, Tp0);
+        cheb_T<PS>(c1.ts, Ts1);
+        cheb_T<PT>(c1.tt, Tt1);
+        cheb_T<PP>(c1.tp, Tp1);
+        for_each_cone(c0.gamma(g), c1.gamma(g), v0, v1, [&](int alpha, bool m0, bool m1) {
+            const int s = __ldg(&slot[(int64_t)kb * g.C + alpha]);
+            if (s < 0) {
+                if (m0 || m1) set_status(status, IFGF_ERR_INTERNAL);
+                return;
+            }
+            float c[NT][4];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+            mma_interp_block<PS, PT, PP, NT>(Ts0, Tt0, Tp0, Ts1, Tt1, Tp1, m0, m1, cchild, s, nrhs, rhs0, cstride, c);
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                if (m0) {
+                    acc[j][0] += rt0.x * c[j][0] - rt0.y * c[j][1];
+                    acc[j][1] += rt0.x * c[j][1] + rt0.y * c[j][0];
+                }
+                if (m1) {
+                    acc[j][2] += rt1.x * c[j][2] - rt1.y * c[j][3];
+                    acc[j][3] += rt1.x * c[j][3] + rt1.y * c[j][2];
+                }
+            }
+        });
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int rl = j * 4 + tq;
+        if (v0) f[rl][n0] = make_float2(acc[j][0], acc[j][1]);
+        if (v1) f[rl][n1] = make_float2(acc[j][2], acc[j][3]);
+    }
+    __syncthreads();
+    // Chebyshev coefficients of every density's node values (phi, theta, s passes)
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int x = threadIdx.x; x < NR * P; x += NTHR) {
+        const int rl = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+        const float2* rw = &f[rl][(qa * PT + qb) * PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const float w = Wp[qc * PP + k];
+            a.x = fmaf(w, rw[k].x, a.x);
+            a.y = fmaf(w, rw[k].y, a.y);
+        }
+        tmp[rl][n] = a;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NR * P; x += NTHR) {
+        const int rl = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < PT; ++jj) {
+            const float w = Wt[qb * PT + jj];
+            const float2 v = tmp[rl][(qa * PT + jj) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        f[rl][n] = a;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NR * P; x += NTHR) {
+        const int rl = x / P, n = x - (x / P) * P;
+        if (rhs0 + rl >= nrhs) continue;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const float w = Ws[qa * PS + i];
+            const float2 v = f[rl][(i * PT + qb) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        cparent[(pc * nrhs + rhs0 + rl) * cstride + n] = a;
+    }
+}
+
+// Interpolation with many densities: one warp per chunk of <= 16 targets of one level-d box (the
+// chunks are built by the plan); for every cousin box, an MMA block per distinct cone.
+template <int PS, int PT, int PP, int NT>
+__global__ void __launch_bounds__(128)
+k_interp_mma(int64_t nchunk, const int32_t* __restrict__ chunk_box, const int32_t* __restrict__ chunk_start,
+             const int32_t* __restrict__ start_d, int64_t N, int sh, const int32_t* __restrict__ pbox_D,
+             const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
+             const int32_t* __restrict__ cs, const float4* __restrict__ off, const int32_t* __restrict__ slot,
+             LevelGrid g, const float2* __restrict__ coef, const float* __restrict__ phtab, float ku, float inv4piu,
+             float2* __restrict__ Is, int cstride, int nrhs, int* __restrict__ status) {
+    const int64_t ch = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (ch >= nchunk) return;  // whole warp leaves together
+    constexpr int NR = 4 * NT;
+    const int rhs0 = blockIdx.y * NR;
+    const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    const int A = chunk_box[ch];
+    const int i0 = chunk_start[ch];
+    const int iend = start_d[A + 1];
+    const int t0 = i0 + gq, t1 = t0 + 8;
+    const bool v0 = t0 < iend, v1 = t1 < iend;
+    const int4 kA = kd[A];
+    const float cscale = (float)(2 << sh);
+    struct Tgt {
+        int4 kl;
+        float4 o;
+        float dax, day, daz, dd;
+    };
+    auto tgt = [&](int i) -> Tgt {
+        Tgt T;
+        T.kl = kD[pbox_D[i]];
+        T.o = off[i];
+        T.dax = (float)((2 * T.kl.x + 1) - ((2 * kA.x + 1) << sh)) + T.o.x;
+        T.day = (float)((2 * T.kl.y + 1) - ((2 * kA.y + 1) << sh)) + T.o.y;
+        T.daz = (float)((2 * T.kl.z + 1) - ((2 * kA.z + 1) << sh)) + T.o.z;
+        T.dd = fmaf(T.dax, T.dax, fmaf(T.day, T.day, T.daz * T.daz));
+        return T;
+    };
+    const Tgt T0 = tgt(v0 ? t0 : i0), T1 = tgt(v1 ? t1 : i0);
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int nc = ncs[A];
+    for (int tc = 0; tc < nc; ++tc) {
+        const int B = cs[(int64_t)A * kMaxCous + tc];
+        const int4 kb = kd[B];
+        const int nx = kA.x - kb.x, ny = kA.y - kb.y, nz = kA.z - kb.z;
+        const int nn = nx * nx + ny * ny + nz * nz;
+        const float cx = cscale * nx, cy = cscale * ny, cz = cscale * nz;
+        const float cn = cscale * sqrtf((float)nn);
+        const float ph0 = __ldg(&phtab[nn]);
+        auto loc = [&](const Tgt& T) -> ConeLocal {
+            const float vx = __fadd_rn((float)((2 * T.kl.x + 1) - ((2 * kb.x + 1) << sh)), T.o.x);
+            const float vy = __fadd_rn((float)((2 * T.kl.y + 1) - ((2 * kb.y + 1) << sh)), T.o.y);
+            const float vz = __fadd_rn((float)((2 * T.kl.z + 1) - ((2 * kb.z + 1) << sh)), T.o.z);
+            return locate_f32(g, vx, vy, vz);
+        };
+        auto green = [&](const Tgt& T, const ConeLocal& cl) -> float2 {
+            const float num = fmaf(2.f, fmaf(cx, T.dax, fmaf(cy, T.day, cz * T.daz)), T.dd);
+            const float corr = __fdividef(num, cl.r + cn);
+            const float2 e = cis_f32(fmaf(ku, corr, ph0));
+            const float w = __fdividef(inv4piu, cl.r);
+            return make_float2(e.x * w, e.y * w);
+        };
+        const ConeLocal c0 = loc(T0), c1 = loc(T1);
+        const float2 G0 = green(T0, c0), G1 = green(T1, c1);
+        float Ts0[PS], Tt0[PT], Tp0[PP], Ts1[PS], Tt1[PT], Tp1[PP];
+        cheb_T<PS>(c0.ts, Ts0);
+        cheb_T<PT>(c0.tt, Tt0);
+        cheb_T<PP>(c0.tp, Tp0);
+        cheb_T<PS>(c1.ts, Ts1);
+        cheb_T<PT>(c1.tt, Tt1);
+        cheb_T<PP>(c1.tp, Tp1);
+        for_each_cone(c0.gamma(g), c1.gamma(g), v0, v1, [&](int alpha, bool m0, bool m1) {
+            const int s = __ldg(&slot[(int64_t)B * g.C + alpha]);
+            if (s < 0) {
+                if (m0 || m1) set_status(status, IFGF_ERR_INTERNAL);
+                return;
+            }
+            float c[NT][4];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
+            mma_interp_block<PS, PT, PP, NT>(Ts0, Tt0, Tp0, Ts1, Tt1, Tp1, m0, m1, coef, s, nrhs, rhs0, cstride, c);
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                if (m0) {
+                    acc[j][0] += G0.x * c[j][0] - G0.y * c[j][1];
+                    acc[j][1] += G0.x * c[j][1] + G0.y * c[j][0];
+                }
+                if (m1) {
+                    acc[j][2] += G1.x * c[j][2] - G1.y * c[j][3];
+                    acc[j][3] += G1.x * c[j][3] + G1.y * c[j][2];
+                }
+            }
+        });
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int rhs = rhs0 + j * 4 + tq;
+        if (rhs >= nrhs) continue;
+        if (v0) {
+            float2* d = Is + (int64_t)rhs * N + t0;
+            *d = make_float2(d->x + acc[j][0], d->y + acc[j][1]);
+        }
+        if (v1) {
+            float2* d = Is + (int64_t)rhs * N + t1;
+            *d = make_float2(d->x + acc[j][2], d->y + acc[j][3]);
+        }
+    }
+}
+
+// Near field and leaf evaluation with a block of NR densities: the kernel value of each pair is
+// computed once and applied to every density of the block.
+template <int NR>
+__global__ void k_near_f32_multi(int64_t N, const int32_t* __restrict__ pboxD, const int4* __restrict__ kD,
+                                 const int32_t* __restrict__ startD, const int32_t* __restrict__ nnb,
+                                 const int32_t* __restrict__ nb, const float4* __restrict__ off,
+                                 const float2* __restrict__ as, float2* __restrict__ Is, float ku, float inv4piu,
+                                 int nrhs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int rhs0 = blockIdx.y * NR;
+    const int l = pboxD[i];
+    const int4 kl = kD[l];
+    const float4 oi = off[i];
+    float2 acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int t = 0; t < nnb[l]; ++t) {
+        const int q = nb[(int64_t)l * kMaxNbr + t];
+        const int4 kq = kD[q];
+        const float bx = (float)(2 * (kl.x - kq.x)) + oi.x;
+        const float by = (float)(2 * (kl.y - kq.y)) + oi.y;
+        const float bz = (float)(2 * (kl.z - kq.z)) + oi.z;
+        for (int j = startD[q]; j < startD[q + 1]; ++j) {
+            if (j == i) continue;
+            const float4 oj = __ldg(&off[j]);
+            const float vx = bx - oj.x, vy = by - oj.y, vz = bz - oj.z;
+            const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+            const float rinv = rsqrtf(r2);
+            const float2 e = cis_f32(ku * (r2 * rinv));
+            const float w = inv4piu * rinv;
+            const float2 gk = make_float2(e.x * w, e.y * w);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (rhs0 + r >= nrhs) break;
+                const float2 aj = __ldg(&as[(int64_t)(rhs0 + r) * N + j]);
+                acc[r] = __ffma2_rn(make_float2(aj.x, aj.x), gk, acc[r]);
+                acc[r] = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(gk.y, gk.x), acc[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r)
+        if (rhs0 + r < nrhs) Is[(int64_t)(rhs0 + r) * N + i] = acc[r];
+}
+
+template <int PS, int PT, int PP, int NR>
+__global__ void k_leaf_f32_multi(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam,
+                                 LevelGrid g, const int32_t* __restrict__ startD, const float4* __restrict__ off,
+                                 const float2* __restrict__ as, int64_t N, float kh, float hinv,
+                                 const float* __restrict__ W, float2* __restrict__ coef, int cstride, int nrhs) {
+    constexpr int P = PS * PT * PP;
+    constexpr int BT = ((P + 31) / 32) * 32;
+    __shared__ float2 f[NR][P], tmp[NR][P];
+    const int cone = blockIdx.x;
+    const int rhs0 = blockIdx.y * NR;
+    const int n = threadIdx.x;
+    const int b = cone_box[cone];
+    if (n < P) {
+        const int gam = cone_gam[cone];
+        const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
+        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+        const float s = g.snode[is * PS + ia];
+        const float st = g.stn[it * PT + ib], ct = g.ctn[it * PT + ib];
+        const float yx = st * g.cpn[ip * PP + ic], yy = st * g.spn[ip * PP + ic], yz = ct;
+        float2 acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = make_float2(0.f, 0.f);
+        for (int j = startD[b]; j < startD[b + 1]; ++j) {
+            const float4 o = __ldg(&off[j]);
+            const float ux = o.x * hinv, uy = o.y * hinv, uz = o.z * hinv;
+            const float wx = fmaf(-s, ux, yx), wy = fmaf(-s, uy, yy), wz = fmaf(-s, uz, yz);
+            const float q = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+            const float rq = rsqrtf(q);
+            const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+            const float yu = fmaf(yx, ux, fmaf(yy, uy, yz * uz));
+            const float ph = kh * __fdividef(fmaf(s, uu, -2.f * yu), fmaf(q, rq, 1.f));
+            const float2 e = cis_f32(ph);
+            const float2 gk = make_float2(e.x * rq, e.y * rq);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                if (rhs0 + r >= nrhs) break;
+                const float2 aj = __ldg(&as[(int64_t)(rhs0 + r) * N + j]);
+                acc[r] = __ffma2_rn(make_float2(aj.x, aj.x), gk, acc[r]);
+                acc[r] = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(gk.y, gk.x), acc[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) f[r][n] = acc[r];
+    }
+    __syncthreads();
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int x = threadIdx.x; x < NR * P; x += BT) {
+        const int rl = x / P, m = x - (x / P) * P;
+        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+        const float2* rw = &f[rl][(qa * PT + qb) * PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const float w = Wp[qc * PP + k];
+            a.x = fmaf(w, rw[k].x, a.x);
+            a.y = fmaf(w, rw[k].y, a.y);
+        }
+        tmp[rl][m] = a;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NR * P; x += BT) {
+        const int rl = x / P, m = x - (x / P) * P;
+        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < PT; ++jj) {
+            const float w = Wt[qb * PT + jj];
+            const float2 v = tmp[rl][(qa * PT + jj) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        f[rl][m] = a;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NR * P; x += BT) {
+        const int rl = x / P, m = x - (x / P) * P;
+        if (rhs0 + rl >= nrhs) continue;
+        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const float w = Ws[qa * PS + i];
+            const float2 v = f[rl][(i * PT + qb) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        coef[((int64_t)cone * nrhs + rhs0 + rl) * cstride + m] = a;
+    }
+}
+
 // ---- driver -------------------------------------------------------------------------------
+// Mixed precision with many densities: tensor-core propagation and interpolation, density-
+// blocked near field and leaf evaluation.
+template <int NT, int PS, int PT, int PP>
+void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
+    constexpr int P = PS * PT * PP;
+    constexpr int BT = ((P + 31) / 32) * 32;
+    constexpr int NR = 4 * NT;
+    constexpr int NRB = 8;  // densities per near-field / leaf block
+    const int64_t N = p.N;
+    const int D = p.D;
+    const double u = p.u;
+    Level& LD = p.L[D];
+    const float ku = (float)(p.kappa * u);
+    const float inv4piu = (float)(1.0 / (4.0 * M_PI * u));
+    float2* as = (float2*)p.a_s;
+    float2* Is = (float2*)p.I_s;
+    const dim3 gN(grid_for(N, kThreads), nrhs);
+    const unsigned rb = (unsigned)((nrhs + NR - 1) / NR);
+    const unsigned rb8 = (unsigned)((nrhs + NRB - 1) / NRB);
+    int cur = 0;
+    {
+        TimedScope ts_(TK_PERM, s);
+        IFGF_LAUNCH(k_perm_in<float2>, gN, kThreads, 0, s, (const float2*)dens, p.perm, N, as);
+    }
+    if (near) {
+        TimedScope ts_(TK_NEAR, s);
+        IFGF_LAUNCH(k_near_f32_multi<NRB>, dim3(grid_for(N, kThreads), rb8), kThreads, 0, s, N, LD.pbox, LD.k, LD.start,
+                    LD.nnb, LD.nb, p.off, as, Is, ku, inv4piu, nrhs);
+    } else {
+        IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * nrhs, s));
+    }
+    if (LD.nc > 0) {
+        TimedScope ts_(TK_LEAF, s);
+        IFGF_LAUNCH((k_leaf_f32_multi<PS, PT, PP, NRB>), dim3((unsigned)LD.nc, rb8), BT, 0, s, LD.cone_box,
+                    LD.cone_gam, LD.g, LD.start, p.off, as, N, (float)(p.kappa * LD.g.h64), 1.0f / LD.g.hg, p.Wf,
+                    (float2*)p.coef[cur], p.cstride, nrhs);
+    }
+    for (int d = D; d >= 3; --d) {
+        Level& L = p.L[d];
+        const int sh = D - d;
+        if (((mask >> d) & 1) && L.nchunk > 0) {
+            TimedScope ts_(TK_INTERP, s);
+            IFGF_LAUNCH((k_interp_mma<PS, PT, PP, NT>), dim3((unsigned)((L.nchunk + 3) / 4), rb), 128, 0, s, L.nchunk,
+                        L.chunk_box, L.chunk_start, L.start, N, sh, LD.pbox, LD.k, L.k, L.ncs, L.cs, p.off, L.slot, L.g,
+                        (const float2*)p.coef[cur], L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status);
+        }
+        if (d == 3) break;
+        Level& Lp = p.L[d - 1];
+        if (Lp.nc > 0) {
+            TimedScope ts_(TK_PROP, s);
+            IFGF_LAUNCH((k_prop_mma<PS, PT, PP, NT>), dim3((unsigned)Lp.nc, rb), 32 * ((P + kChunk - 1) / kChunk), 0, s,
+                        Lp.nc, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, Lp.g, L.k, L.slot, L.g,
+                        (const float2*)p.coef[cur], (float2*)p.coef[1 - cur], sh, ku, p.Wf, p.cstride, nrhs,
+                        p.d_status);
+        }
+        cur = 1 - cur;
+    }
+    {
+        TimedScope ts_(TK_PERM, s);
+        IFGF_LAUNCH(k_perm_out<float2>, gN, kThreads, 0, s, Is, p.perm, N, (float2*)out);
+    }
+}
+
+template <int PS, int PT, int PP>
+void run_apply_multi(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
+    if constexpr (PS == 3 && PT == 5 && PP == 5) {
+        if (nrhs <= 8)
+            run_apply_multi_nt<2, PS, PT, PP>(p, dens, nrhs, out, s, near, mask);
+        else if (nrhs <= 16)
+            run_apply_multi_nt<4, PS, PT, PP>(p, dens, nrhs, out, s, near, mask);
+        else
+            run_apply_multi_nt<8, PS, PT, PP>(p, dens, nrhs, out, s, near, mask);
+    } else {
+        fail(IFGF_ERR_UNSUPPORTED, "tensor-core path built for orders (3,5,5) only");
+    }
+}
+
 template <int PS, int PT, int PP>
 void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
     constexpr int P = PS * PT * PP;
@@ -716,7 +1200,9 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
     const double HD = std::ldexp(p.H1, 1 - D);
     Level& LD = p.L[D];
     int cur = 0;
-    if (mixed) {
+    if (mixed && nrhs >= kMmaMinRhs && PS == 3 && PT == 5 && PP == 5) {
+        run_apply_multi<PS, PT, PP>(p, dens, nrhs, out, s, near, mask);
+    } else if (mixed) {
         const float ku = (float)(p.kappa * u);
         const float inv4piu = (float)(1.0 / (4.0 * M_PI * u));
         float2* as = (float2*)p.a_s;
@@ -827,12 +1313,19 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
 }  // namespace
 
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
-    if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
-        run_apply<3, 5, 5>(p, dens, nrhs, out, s, near, mask);
-    else if (p.Ps == 5 && p.Pt == 7 && p.Pp == 7)
-        run_apply<5, 7, 7>(p, dens, nrhs, out, s, near, mask);
-    else
-        fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
+    // densities in blocks of at most rhs_block, one level sweep per block
+    const size_t csz = p.precision == IFGF_PREC_MIXED ? sizeof(float2) : sizeof(double2);
+    for (int r0 = 0; r0 < nrhs; r0 += p.rhs_block) {
+        const int nb = std::min(p.rhs_block, nrhs - r0);
+        const void* d = static_cast<const char*>(dens) + (size_t)r0 * p.N * csz;
+        void* o = static_cast<char*>(out) + (size_t)r0 * p.N * csz;
+        if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
+            run_apply<3, 5, 5>(p, d, nb, o, s, near, mask);
+        else if (p.Ps == 5 && p.Pt == 7 && p.Pp == 7)
+            run_apply<5, 7, 7>(p, d, nb, o, s, near, mask);
+        else
+            fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
+    }
 }
 
 }  // namespace ifgf

@@ -86,6 +86,10 @@ struct Level {
     int32_t* tab_k = nullptr;      // [n_gam*8] distinct child cones of the row (K <= kTabList)
     int32_t* tab_list = nullptr;   // [n_gam*8][kTabList] their child cone indices
     int16_t* tab_perm = nullptr;   // [n_gam*8*P] nodes of the row ordered by child cone (stable)
+    // Target chunks of <= 16 points of one box (tensor-core interpolation with many densities).
+    int64_t nchunk = 0;
+    int32_t* chunk_box = nullptr;
+    int32_t* chunk_start = nullptr;
 };
 constexpr int kTabList = 32;
 
@@ -97,6 +101,7 @@ struct Plan {
     int cstride = 76;              // complex entries per cone and density vector
     int precision = IFGF_PREC_MIXED;
     int max_nrhs = 1;
+    int rhs_block = 1;             // densities per level sweep (coefficient buffers hold this many)
     double a[3] = {0, 0, 0};
     double H1 = 0, u = 0;
     int device = 0;
@@ -503,6 +508,93 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// ---- tensor-core helpers (warp-level mma.sync, TF32, 3xTF32 split precision) ----------------
+// Fragment layout of mma.m16n8k8 (row.col), g = lane / 4, t = lane % 4:
+//   A (16x8):  a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
+//   B (8x8):   b0 (t, g), b1 (t+4, g)
+//   C (16x8):  c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// x = hi + lo with both parts representable in TF32 (the split of 3xTF32 products)
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+    hi = tf32_bits(x);
+    lo = tf32_bits(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// C += A B with A = ah + al, B = bh + bl to FP32 accuracy: al bh + ah bl + ah bh.
+__device__ __forceinline__ void mma_3xtf32(float (&c)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                           const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+    mma_tf32(c, al, bh);
+    mma_tf32(c, ah, bl);
+    mma_tf32(c, ah, bh);
+}
+
+// Multi-density interpolant contraction for one warp: 16 points (rows r0 = g, r1 = g + 8,
+// whose Chebyshev values this thread holds), the coefficient block of one cone for 4*NT
+// densities starting at rhs0 (row p = coefficient index, columns (density, re/im)), rows whose
+// mask bit is clear contribute zero.  c[j] receives the C fragment of n-tile j.
+template <int N>
+__device__ __forceinline__ float pick(const float (&v)[N], int i) {  // v[i] without local memory
+    float r = v[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) r = (i == k) ? v[k] : r;
+    return r;
+}
+
+template <int PS, int PT, int PP, int NT>
+__device__ __forceinline__ void mma_interp_block(const float (&Ts0)[PS], const float (&Tt0)[PT],
+                                                 const float (&Tp0)[PP], const float (&Ts1)[PS],
+                                                 const float (&Tt1)[PT], const float (&Tp1)[PP], bool row0,
+                                                 bool row1, const float2* __restrict__ coef, int64_t cone_base,
+                                                 int nrhs, int rhs0, int cstride, float (&c)[NT][4]) {
+    constexpr int P = PS * PT * PP;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    // density columns of this thread in every n-tile: (rhs, re/im) = (rhs0 + (8j + g)/2, g & 1)
+    const float* blk[NT];
+    bool colok[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int rhs = rhs0 + ((j * 8 + g) >> 1);
+        colok[j] = rhs < nrhs;
+        blk[j] = reinterpret_cast<const float*>(coef + (cone_base * nrhs + (colok[j] ? rhs : 0)) * cstride) + (g & 1);
+    }
+#pragma unroll 1
+    for (int kk = 0; kk < (P + 7) / 8; ++kk) {
+        const int p0 = kk * 8 + t, p1 = p0 + 4;
+        const int a0 = p0 / (PT * PP), b0 = (p0 / PP) % PT, q0 = p0 % PP;
+        const int a1 = p1 / (PT * PP), b1 = (p1 / PP) % PT, q1 = p1 % PP;
+        const bool ok0 = p0 < P, ok1 = p1 < P;
+        const float A0 = (row0 && ok0) ? pick(Ts0, a0) * pick(Tt0, b0) * pick(Tp0, q0) : 0.f;
+        const float A1 = (row1 && ok0) ? pick(Ts1, a0) * pick(Tt1, b0) * pick(Tp1, q0) : 0.f;
+        const float A2 = (row0 && ok1) ? pick(Ts0, a1) * pick(Tt0, b1) * pick(Tp0, q1) : 0.f;
+        const float A3 = (row1 && ok1) ? pick(Ts1, a1) * pick(Tt1, b1) * pick(Tp1, q1) : 0.f;
+        uint32_t ah[4], al[4];
+        tf32_split(A0, ah[0], al[0]);
+        tf32_split(A1, ah[1], al[1]);
+        tf32_split(A2, ah[2], al[2]);
+        tf32_split(A3, ah[3], al[3]);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const float B0 = (colok[j] && ok0) ? __ldg(blk[j] + 2 * p0) : 0.f;
+            const float B1 = (colok[j] && ok1) ? __ldg(blk[j] + 2 * p1) : 0.f;
+            uint32_t bh[2], bl[2];
+            tf32_split(B0, bh[0], bl[0]);
+            tf32_split(B1, bh[1], bl[1]);
+            mma_3xtf32(c[j], ah, al, bh, bl);
+        }
+    }
+}
 
 // Morton interleave of three 21-bit coordinates (bit 3b = x_b, 3b+1 = y_b, 3b+2 = z_b).
 __host__ __device__ __forceinline__ uint64_t spread3(uint32_t v) {

@@ -222,3 +222,48 @@ def test_full_size_sphere64_sampled(prec):
     if prec == "mixed":
         op = oracle.Plan(pts, kappa)
         assert_same_tree(gp, op)
+
+
+@pytest.mark.parametrize("nrhs", [4, 12, 32])
+@pytest.mark.parametrize("shape", ["sphere", "oblate"])
+def test_many_densities_tensor_core_path(nrhs, shape):
+    """nrhs >= 4 runs the tensor-core (3xTF32 mma.sync) propagation and interpolation; every
+    density must match the CPU IFGF as the single-density path does, and agree with it."""
+    n = 8000
+    pts = W.fibonacci_sphere(n) if shape == "sphere" else W.spheroid(n, 0.5, 0.125, seed=31)
+    kappa = 2 * math.pi * 5
+    A = W.densities(n, nrhs, 21)
+    ref = oracle.Plan(pts, kappa).apply(A)
+    gp = _plan(pts, kappa, precision="mixed", max_nrhs=nrhs)
+    got = _apply(gp, A, "mixed")
+    assert gp.status() == 0
+    for r in range(nrhs):
+        assert oracle.rel_l2(got[r], ref[r]) < 3e-5, r
+    single = _apply(_plan(pts, kappa, precision="mixed"), A[nrhs - 1], "mixed")[0]
+    assert oracle.rel_l2(got[nrhs - 1], single) < 2e-5
+
+
+@pytest.mark.parametrize("stage", ["near", "leaf_level", "top_level"])
+def test_many_densities_stages(stage):
+    w = W.make("sphere4")
+    pts, kappa = w.points(), w.kappa
+    A = W.densities(w.n, 8, 3)
+    op = oracle.Plan(pts, kappa)
+    gp = _plan(pts, kappa, precision="mixed", max_nrhs=8)
+    near, mask = {"near": (True, 0), "leaf_level": (False, 1 << op.D), "top_level": (False, 1 << 3)}[stage]
+    ref = op.apply(A, near=near, level_mask=mask)
+    got = _apply(gp, A, "mixed", near=near, level_mask=mask)
+    for r in range(8):
+        assert oracle.rel_l2(got[r], ref[r]) < 3e-5
+
+
+def test_density_blocks_equal_one_sweep():
+    """With rhs_block smaller than nrhs, the levels are swept once per block of densities; the
+    result is the same as one sweep over all densities."""
+    pts = W.fibonacci_sphere(5000)
+    kappa = 2 * math.pi * 4
+    A = W.densities(5000, 10, 8)
+    full = _apply(_plan(pts, kappa, precision="mixed", max_nrhs=10), A, "mixed")
+    blocked = _apply(_plan(pts, kappa, precision="mixed", max_nrhs=10, rhs_block=4), A, "mixed")
+    for r in range(10):
+        assert oracle.rel_l2(blocked[r], full[r]) < 2e-5
