@@ -403,22 +403,28 @@ k_prop_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __
 
 // Propagation from the node tables of the parent level: the geometry of every (cone index,
 // child octant, node) was computed once at plan time, so an evaluation is a table read, the
-// child cone's slot, the interpolant contraction and the complex ratio.
+// child cone's slot, the interpolant contraction and the complex ratio. A thread evaluates one
+// segment: up to kSegLen nodes of one (parent cone, child) pair that fall in the same child
+// cone, sharing the coefficient loads of that cone.
+constexpr int kSegCones = 8;     // parent cones per block
+constexpr int kSegThreads = 128;
 template <int PS, int PT, int PP>
-__global__ void __launch_bounds__(kPropThreads, 5)
+__global__ void __launch_bounds__(kSegThreads, 3)
 k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
                const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
                const int32_t* __restrict__ slot, int C, const float4* __restrict__ tab_t,
                const float2* __restrict__ tab_r, const int32_t* __restrict__ tab_k,
                const int32_t* __restrict__ tab_list, const int16_t* __restrict__ tab_perm,
-               const float2* __restrict__ cchild,
-               float2* __restrict__ cparent, const float* __restrict__ W, int cstride, int nrhs,
-               int* __restrict__ status) {
+               const int32_t* __restrict__ tab_nseg, const int32_t* __restrict__ tab_seg,
+               const float2* __restrict__ cchild, float2* __restrict__ cparent, const float* __restrict__ W,
+               int cstride, int nrhs, int* __restrict__ status) {
     constexpr int P = PS * PT * PP;
-    constexpr int NC = kPropCones;
+    constexpr int NC = kSegCones;
+    constexpr int R = kSegLen;
+    // vals[c][ch][n]: child ch's contribution at node n of cone c; after the sum over children,
+    // vals[c][0] holds the node values and vals[c][1] the first transform stage
     __shared__ float2 vals[NC][8][P];
-    __shared__ float2 f[NC][P], tmp[NC][P];
-    __shared__ int s_off[NC + 1], s_kb0[NC], s_row[NC][8];
+    __shared__ int s_goff[NC * 8 + 1], s_kb0[NC], s_nch[NC], s_row[NC][8];
     __shared__ int s_slot[NC][8][kTabList];
     const int tid = threadIdx.x;
     const int r = blockIdx.y;
@@ -439,22 +445,24 @@ k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
                 s_row[c][ch] = g8 + ((kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2));
             }
         }
-        s_off[c + 1] = nch * P;
+        s_nch[c] = nch;
+    }
+    __syncthreads();
+    if (tid < NC * 8) {
+        const int c = tid / 8, ch = tid % 8;
+        s_goff[tid + 1] = ch < s_nch[c] ? __ldg(&tab_nseg[s_row[c][ch]]) : 0;
     }
     __syncthreads();
     if (tid == 0) {
-        s_off[0] = 0;
-        for (int c = 0; c < NC; ++c) s_off[c + 1] += s_off[c];
+        s_goff[0] = 0;
+        for (int g = 0; g < NC * 8; ++g) s_goff[g + 1] += s_goff[g];
     }
     // child-cone slots of every (cone, child) group, once per block; their coefficient blocks
     // are prefetched into L2 while the slots resolve
-    for (int x = tid; x < NC * 8 * kTabList; x += kPropThreads) {
+    for (int x = tid; x < NC * 8 * kTabList; x += kSegThreads) {
         const int k = x % kTabList, g = x / kTabList;
         const int c = g / 8, ch = g % 8;
-        const int64_t pc = pc0 + c;
-        if (pc >= ncp) continue;
-        const int jb_n = pcstart[pcone_box[pc] + 1] - s_kb0[c];
-        if (ch >= jb_n) continue;
+        if (ch >= s_nch[c]) continue;
         const int row = s_row[c][ch];
         if (k >= __ldg(&tab_k[row])) continue;
         const int sl = __ldg(&slot[(int64_t)(s_kb0[c] + ch) * C + __ldg(&tab_list[(int64_t)row * kTabList + k])]);
@@ -466,73 +474,83 @@ k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
         }
     }
     __syncthreads();
-    const int total = s_off[NC];
-    for (int item = tid; item < total; item += kPropThreads) {
-        int c = 0;
+    const int total = s_goff[NC * 8];
+    for (int item = tid; item < total; item += kSegThreads) {
+        int g = 0;  // last group with s_goff[g] <= item
 #pragma unroll
-        for (int k = 1; k < NC; ++k) c += item >= s_off[k];
-        const int rem = item - s_off[c];
-        const int ch = rem / P, j = rem - ch * P;
+        for (int step = 32; step >= 1; step >>= 1)
+            if (g + step < NC * 8 && s_goff[g + step] <= item) g += step;
+        const int c = g / 8, ch = g % 8;
         const int64_t rowP = (int64_t)s_row[c][ch] * P;
-        const int n = __ldg(&tab_perm[rowP + j]);  // nodes ordered by child cone: warps share blocks
-        const int64_t e = rowP + n;
-        const float4 t4 = __ldg(&tab_t[e]);
-        const float2 ratio = __ldg(&tab_r[e]);
-        const int kl = __float_as_int(t4.w);
+        const int sg = __ldg(&tab_seg[rowP + (item - s_goff[g])]);
+        const int j0 = sg & 0xff, len = (sg >> 8) & 0xff, kl = sg >> 16;
         const int s = (unsigned)kl < (unsigned)kTabList ? s_slot[c][ch][kl] : -1;
-        float2 t = make_float2(0.f, 0.f);
+        float ts[R], tt[R], tp[R];
+        float2 ratio[R], F[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int64_t e = rowP + j0 + min(q, len - 1);  // short segments repeat their last node
+            const float4 t4 = __ldg(&tab_t[e]);
+            ts[q] = t4.x;
+            tt[q] = t4.y;
+            tp[q] = t4.z;
+            ratio[q] = __ldg(&tab_r[e]);
+        }
         if (s < 0) {
             set_status(status, IFGF_ERR_INTERNAL);
+#pragma unroll
+            for (int q = 0; q < R; ++q) F[q] = make_float2(0.f, 0.f);
         } else {
-            const float2 F = interp_f32<PS, PT, PP>(cchild + ((int64_t)s * nrhs + r) * cstride, t4.x, t4.y, t4.z);
-            t = cmul(F, ratio);
+            interp_f32_seg<PS, PT, PP, R>(cchild + ((int64_t)s * nrhs + r) * cstride, ts, tt, tp, F);
         }
-        vals[c][ch][n] = t;
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (q < len) vals[c][ch][__ldg(&tab_perm[rowP + j0 + q])] = cmul(F[q], ratio[q]);
     }
     __syncthreads();
     const float* Ws = W;
     const float* Wt = W + PS * PS;
     const float* Wp = Wt + PT * PT;
-    for (int x = tid; x < NC * P; x += kPropThreads) {
+    for (int x = tid; x < NC * P; x += kSegThreads) {
         const int c = x / P, n = x - (x / P) * P;
-        const int nch = (s_off[c + 1] - s_off[c]) / P;
+        const int nch = s_nch[c];
         float2 a = make_float2(0.f, 0.f);
         for (int ch = 0; ch < nch; ++ch) {
             a.x += vals[c][ch][n].x;
             a.y += vals[c][ch][n].y;
         }
-        f[c][n] = a;
+        vals[c][0][n] = a;
     }
     __syncthreads();
-    for (int x = tid; x < NC * P; x += kPropThreads) {
+    for (int x = tid; x < NC * P; x += kSegThreads) {
         const int c = x / P, n = x - (x / P) * P;
         const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
         float2 acc = make_float2(0.f, 0.f);
-        const float2* rw = &f[c][(qa * PT + qb) * PP];
+        const float2* rw = &vals[c][0][(qa * PT + qb) * PP];
 #pragma unroll
         for (int k = 0; k < PP; ++k) {
             const float w = Wp[qc * PP + k];
             acc.x = fmaf(w, rw[k].x, acc.x);
             acc.y = fmaf(w, rw[k].y, acc.y);
         }
-        tmp[c][n] = acc;
+        vals[c][1][n] = acc;
     }
     __syncthreads();
-    for (int x = tid; x < NC * P; x += kPropThreads) {
+    for (int x = tid; x < NC * P; x += kSegThreads) {
         const int c = x / P, n = x - (x / P) * P;
         const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < PT; ++j) {
             const float w = Wt[qb * PT + j];
-            const float2 v = tmp[c][(qa * PT + j) * PP + qc];
+            const float2 v = vals[c][1][(qa * PT + j) * PP + qc];
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
         }
-        f[c][n] = acc;
+        vals[c][0][n] = acc;
     }
     __syncthreads();
-    for (int x = tid; x < NC * P; x += kPropThreads) {
+    for (int x = tid; x < NC * P; x += kSegThreads) {
         const int c = x / P, n = x - (x / P) * P;
         const int64_t pc = pc0 + c;
         if (pc >= ncp) continue;
@@ -541,7 +559,7 @@ k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
             const float w = Ws[qa * PS + i];
-            const float2 v = f[c][(i * PT + qb) * PP + qc];
+            const float2 v = vals[c][0][(i * PT + qb) * PP + qc];
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
         }
@@ -1239,11 +1257,14 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                 }
             if (d == 3) break;
             Level& Lp = p.L[d - 1];
-            if (Lp.nc > 0 && Lp.n_gam > 0) {
+            if (Lp.nc > 0 && Lp.n_gam > 0 && PS * PT * PP <= 75) {  // tables are built for (3,5,5) only
                 TimedScope ts_(TK_PROP, s);
-                IFGF_LAUNCH((k_prop_tab_f32<PS, PT, PP>), dim3((unsigned)((Lp.nc + kPropCones - 1) / kPropCones), nrhs),
-                            kPropThreads, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, L.slot, L.g.C,
-                            Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, (const float2*)p.coef[cur],
+                constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
+                              TP = PS * PT * PP <= 75 ? PP : 5;
+                IFGF_LAUNCH((k_prop_tab_f32<TS, TT, TP>), dim3((unsigned)((Lp.nc + kSegCones - 1) / kSegCones), nrhs),
+                            kSegThreads, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, L.slot, L.g.C,
+                            Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg,
+                            (const float2*)p.coef[cur],
                             (float2*)p.coef[1 - cur], p.Wf, p.cstride, nrhs, p.d_status);
             } else if (Lp.nc > 0)
                 {

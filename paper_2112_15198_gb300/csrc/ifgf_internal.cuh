@@ -81,17 +81,23 @@ struct Level {
     int32_t n_gam = 0;             // rows (0: no tables, the kernels compute the geometry)
     int32_t* gam_list = nullptr;   // [n_gam] gamma of each row
     int32_t* cone_gidx = nullptr;  // [nc] row of each relevant cone
+    // Entries of a row are stored in the order of their child cone (stable in the node index).
     float4* tab_t = nullptr;       // (t_s, t_theta, t_phi, position of the child cone in the row's list)
     float2* tab_r = nullptr;       // G(x, x_k) / G(x, x_j)
     int32_t* tab_k = nullptr;      // [n_gam*8] distinct child cones of the row (K <= kTabList)
     int32_t* tab_list = nullptr;   // [n_gam*8][kTabList] their child cone indices
-    int16_t* tab_perm = nullptr;   // [n_gam*8*P] nodes of the row ordered by child cone (stable)
+    int16_t* tab_perm = nullptr;   // [n_gam*8*P] node index of each sorted entry
+    // Segments: runs of <= kSegLen sorted entries with one child cone, packed as
+    // first entry | length << 8 | list position << 16.
+    int32_t* tab_nseg = nullptr;   // [n_gam*8]
+    int32_t* tab_seg = nullptr;    // [n_gam*8*P]
     // Target chunks of <= 16 points of one box (tensor-core interpolation with many densities).
     int64_t nchunk = 0;
     int32_t* chunk_box = nullptr;
     int32_t* chunk_start = nullptr;
 };
 constexpr int kTabList = 32;
+constexpr int kSegLen = 8;  // nodes of one child cone evaluated by one thread
 
 struct Plan {
     int64_t N = 0;
@@ -416,6 +422,77 @@ __device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float
             acc = __ffma2_rn(aa, make_float2(Ts[a], Ts[a]), acc);
         }
         return acc;
+    }
+}
+
+// The contraction of interp_f32 for R points of one cone: every coefficient row is loaded
+// once and applied to all R points, so the coefficient bytes moved into registers per point
+// drop by R. Row (a, b) enters point q with weight T_a(ts_q) T_b(tt_q).
+template <int PS, int PT, int PP, int R>
+__device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, const float* ts, const float* tt,
+                                               const float* tp, float2* out) {
+    float Ts[R][PS], Tt[R][PT], Tp[R][PP];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        cheb_T<PS>(ts[q], Ts[q]);
+        cheb_T<PT>(tt[q], Tt[q]);
+        cheb_T<PP>(tp[q], Tp[q]);
+        out[q] = make_float2(0.f, 0.f);
+    }
+    auto fold = [&](int rr, const float2* row) {
+        const int a = rr / PT, b = rr - (rr / PT) * PT;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            float2 bb = row[0];
+#pragma unroll
+            for (int k = 1; k < PP; ++k) bb = __ffma2_rn(row[k], make_float2(Tp[q][k], Tp[q][k]), bb);
+            const float w = Ts[q][a] * Tt[q][b];
+            out[q] = __ffma2_rn(bb, make_float2(w, w), out[q]);
+        }
+    };
+    constexpr int NR = PS * PT;
+    if constexpr (PP == 5) {
+        const float4* c4 = reinterpret_cast<const float4*>(c);
+#pragma unroll
+        for (int m = 0; m < NR / 2; ++m) {
+            const float4 v0 = __ldg(c4 + 5 * m + 0), v1 = __ldg(c4 + 5 * m + 1), v2 = __ldg(c4 + 5 * m + 2);
+            const float4 v3 = __ldg(c4 + 5 * m + 3), v4 = __ldg(c4 + 5 * m + 4);
+            const float2 r0[5] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                  make_float2(v1.z, v1.w), make_float2(v2.x, v2.y)};
+            const float2 r1[5] = {make_float2(v2.z, v2.w), make_float2(v3.x, v3.y), make_float2(v3.z, v3.w),
+                                  make_float2(v4.x, v4.y), make_float2(v4.z, v4.w)};
+            fold(2 * m, r0);
+            fold(2 * m + 1, r1);
+        }
+        if constexpr (NR % 2 == 1) {
+            const float4 v0 = __ldg(c4 + 5 * (NR / 2) + 0), v1 = __ldg(c4 + 5 * (NR / 2) + 1);
+            const float2 v2 = __ldg(c + 10 * (NR / 2) + 4);
+            const float2 r0[5] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                  make_float2(v1.z, v1.w), v2};
+            fold(NR - 1, r0);
+        }
+    } else {
+#pragma unroll 1
+        for (int rr = 0; rr < NR; ++rr) {
+            float2 row[PP];
+#pragma unroll
+            for (int k = 0; k < PP; ++k) row[k] = __ldg(c + rr * PP + k);
+            // rr is not a compile-time constant here: weights by explicit selection
+            const int a = rr / PT, b = rr - (rr / PT) * PT;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                float2 bb = row[0];
+#pragma unroll
+                for (int k = 1; k < PP; ++k) bb = __ffma2_rn(row[k], make_float2(Tp[q][k], Tp[q][k]), bb);
+                float wa = Ts[q][0], wb = Tt[q][0];
+#pragma unroll
+                for (int i = 1; i < PS; ++i) wa = a == i ? Ts[q][i] : wa;
+#pragma unroll
+                for (int i = 1; i < PT; ++i) wb = b == i ? Tt[q][i] : wb;
+                const float w = wa * wb;
+                out[q] = __ffma2_rn(bb, make_float2(w, w), out[q]);
+            }
+        }
     }
 }
 

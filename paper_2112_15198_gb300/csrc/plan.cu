@@ -340,16 +340,19 @@ __global__ void k_node_tables(int64_t total, const int32_t* __restrict__ gam_lis
 // Distinct child cones of each table row (gamma, octant): the list, and each node's position in
 // it (replacing the cone index in tab_t.w).  Rows are built from the 75-node classification, so
 // K <= 75; the build rejects K > kTabList (the plan then computes that level's geometry).
-__global__ void k_node_lists(int P, float4* __restrict__ tab_t, int32_t* __restrict__ tab_k,
-                             int32_t* __restrict__ tab_list, int16_t* __restrict__ tab_perm,
-                             int* __restrict__ overflow) {
+__global__ void k_node_lists(int P, float4* __restrict__ tab_t, float2* __restrict__ tab_r,
+                             int32_t* __restrict__ tab_k, int32_t* __restrict__ tab_list,
+                             int16_t* __restrict__ tab_perm, int32_t* __restrict__ tab_nseg,
+                             int32_t* __restrict__ tab_seg, int* __restrict__ overflow) {
     __shared__ int alpha[128];  // child cone of each node
     __shared__ int first[128];  // 1 if the node is the first with its child cone
     __shared__ int idx[128];    // list position, defined where first[] is set
     __shared__ int kpos[128];   // list position of every node
+    __shared__ int segst[128];  // 1 if the sorted entry starts a segment
     const int64_t row = blockIdx.x;
     const int n = threadIdx.x;
     if (n < P) alpha[n] = __float_as_int(tab_t[row * P + n].w);
+    segst[n] = 0;
     __syncthreads();
     if (n < P) {
         int f = 1;
@@ -377,15 +380,39 @@ __global__ void k_node_lists(int P, float4* __restrict__ tab_t, int32_t* __restr
         kpos[n] = k;
     }
     __syncthreads();
+    // stable position of node n among the row's nodes ordered by child cone; the run of its
+    // child cone starts at `before` and holds `cnt` entries
+    int k = 0, pos = 0, before = 0, cnt = 0;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 rr = make_float2(0.f, 0.f);
     if (n < P) {
-        const int k = kpos[n];
-        float4 t = tab_t[row * P + n];
+        k = kpos[n];
+        for (int m = 0; m < P; ++m) {
+            pos += (kpos[m] < k) || (kpos[m] == k && m < n);
+            before += kpos[m] < k;
+            cnt += kpos[m] == k;
+        }
+        t = tab_t[row * P + n];
         t.w = __int_as_float(k);
-        tab_t[row * P + n] = t;
-        // stable position of node n among the row's nodes ordered by child cone
-        int pos = 0;
-        for (int m = 0; m < P; ++m) pos += (kpos[m] < k) || (kpos[m] == k && m < n);
+        rr = tab_r[row * P + n];
+        segst[pos] = (pos - before) % kSegLen == 0;
+    }
+    __syncthreads();  // every entry is read before any is moved
+    if (n < P) {
+        tab_t[row * P + pos] = t;
+        tab_r[row * P + pos] = rr;
         tab_perm[row * P + pos] = (int16_t)n;
+        if (segst[pos]) {
+            int sidx = 0;
+            for (int j = 0; j < pos; ++j) sidx += segst[j];
+            const int len = min(kSegLen, before + cnt - pos);
+            tab_seg[row * P + sidx] = pos | (len << 8) | (k << 16);
+        }
+        if (n == 0) {
+            int ns = 0;
+            for (int j = 0; j < P; ++j) ns += segst[j];
+            tab_nseg[row] = ns;
+        }
     }
 }
 
@@ -571,7 +598,7 @@ void build_node_tables(Plan& p, int dp) {
     const int32_t n_gam = read_one(p, pos + (C - 1)) + read_one(p, flags + (C - 1));
     const int64_t entries = (int64_t)n_gam * 8 * p.P;
     const double sharing = (double)Lp.nc / std::max(1, n_gam);
-    if (sharing >= 4.0 && entries * 24 <= ((int64_t)1 << 30)) {
+    if (sharing >= 4.0 && entries * 30 <= ((int64_t)1 << 30)) {
         Lp.n_gam = n_gam;
         Lp.gam_list = dalloc<int32_t>(p, n_gam);
         Lp.cone_gidx = dalloc<int32_t>(p, Lp.nc);
@@ -585,10 +612,12 @@ void build_node_tables(Plan& p, int dp) {
         Lp.tab_k = dalloc<int32_t>(p, (size_t)n_gam * 8);
         Lp.tab_list = dalloc<int32_t>(p, (size_t)n_gam * 8 * kTabList);
         Lp.tab_perm = dalloc<int16_t>(p, (size_t)entries);
+        Lp.tab_nseg = dalloc<int32_t>(p, (size_t)n_gam * 8);
+        Lp.tab_seg = dalloc<int32_t>(p, (size_t)entries);
         int* ovf = dalloc<int>(p, 1);
         IFGF_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), p.stream));
-        IFGF_LAUNCH(k_node_lists, (unsigned)(n_gam * 8), 128, 0, p.stream, p.P, Lp.tab_t, Lp.tab_k, Lp.tab_list,
-                    Lp.tab_perm, ovf);
+        IFGF_LAUNCH(k_node_lists, (unsigned)(n_gam * 8), 128, 0, p.stream, p.P, Lp.tab_t, Lp.tab_r, Lp.tab_k,
+                    Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, ovf);
         const int overflow = read_one(p, ovf);
         dfree_ptr(p, ovf);
         if (overflow) {  // some row has more distinct child cones than a list holds: no tables
@@ -599,6 +628,8 @@ void build_node_tables(Plan& p, int dp) {
             dfree_ptr(p, Lp.tab_k);
             dfree_ptr(p, Lp.tab_list);
             dfree_ptr(p, Lp.tab_perm);
+            dfree_ptr(p, Lp.tab_nseg);
+            dfree_ptr(p, Lp.tab_seg);
             Lp.n_gam = 0;
         }
     }
