@@ -323,10 +323,23 @@ def main():
     dom_ms, dom_n = kinds[dom]
     per_launch_flops = flops[dom] * args.steps / dom_n
     achieved = per_launch_flops / (dom_ms / dom_n / 1e3) / 1e12
-    kernel_name = {"prop": "k_prop_f32", "interp": "k_interp_f32", "leaf": "k_leaf_f32", "near": "k_near_f32"}[dom]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / PEAK_FP32_TFLOPS, "traffic": traffic_record(kernel_name), "kernel": kernel_name,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (derived, not measured)",
+    kernel_name = {"prop": "k_prop_tab_f32" if args.precision == "mixed" else "k_prop_f64",
+                   "interp": "k_interp_f32", "leaf": "k_leaf_f32", "near": "k_near_f32"}[dom]
+    # FP32 (FP64) FMA throughput measured on this device by the probe kernels
+    try:
+        peaks = ifgf.measure_peaks()
+        if args.precision == "mixed":
+            peak = max(peaks["fp32_ffma_tflops"], peaks["fp32x2_ffma2_tflops"])
+            peak_source = "measured: FP32 FFMA/FFMA2 probe on this GPU (of measured)"
+        else:
+            peak = peaks["fp64_tflops"]
+            peak_source = "measured: FP64 DFMA probe on this GPU (of measured)"
+    except Exception as exc:  # the probe library is optional for the line itself
+        peaks, peak = {"error": str(exc)}, PEAK_FP32_TFLOPS
+        peak_source = "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (derived, not measured)"
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_record(kernel_name), "kernel": kernel_name,
+                "peak_source": peak_source, "peaks_measured": peaks,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
                 "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kt.items()}}
 

@@ -133,6 +133,21 @@ def launch_count() -> int:
     return int(load().ifgf_launch_count())
 
 
+def measure_peaks() -> dict:
+    """Measured throughputs of the current device (separate probe library): FP32 FFMA and
+    FP32x2 FFMA2 TFLOP/s, FP64 TFLOP/s, MUFU sine Gop/s, TF32 mma.sync TFLOP/s, SM count."""
+    load()
+    lib = ctypes.CDLL(_build.PEAKS_LIB)
+    lib.ifgf_peaks_measure.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    lib.ifgf_peaks_measure.restype = ctypes.c_int
+    out = (ctypes.c_double * 6)()
+    rc = lib.ifgf_peaks_measure(out)
+    if rc != 0:
+        raise IFGFError(3, f"peak probes failed with CUDA error {rc}")
+    keys = ("fp32_ffma_tflops", "fp32x2_ffma2_tflops", "fp64_tflops", "mufu_sin_gops", "tf32_mma_sync_tflops", "sms")
+    return {k: float(v) for k, v in zip(keys, out)}
+
+
 TIMING_KINDS = ("perm", "near", "leaf", "prop", "interp", "plan")
 
 

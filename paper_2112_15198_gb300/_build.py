@@ -18,6 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, f"libifgf_{platform.machine()}.so")
 SOURCES = ["util.cu", "plan.cu", "apply.cu", "api.cu", "noalloc.cu", "batch.cu"]
+# throughput probes for the roofline denominators (a library of their own)
+PEAKS_LIB = os.path.join(BUILD, f"libifgf_peaks_{platform.machine()}.so")
+PEAKS_SOURCES = ["peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -35,9 +38,9 @@ def _deps_mtime() -> float:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Build the library if a source is newer than it; return its path."""
+    """Build the libraries if a source is newer than them; return the IFGF library's path."""
     os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    if not force and all(os.path.exists(f) and os.path.getmtime(f) >= _deps_mtime() for f in (LIB, PEAKS_LIB)):
         return LIB
     nvcc = _nvcc()
     objs = []
@@ -54,13 +57,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + len(PEAKS_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES + PEAKS_SOURCES))
+    for lib, lo in ((LIB, objs[:len(SOURCES)]), (PEAKS_LIB, objs[len(SOURCES):])):
+        tmp = lib + f".tmp{os.getpid()}"
+        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *lo], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 
