@@ -880,6 +880,167 @@ k_prop_mma(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __
     }
 }
 
+// Propagation with many densities from the node tables (orders (3,5,5)). For a child cone
+// alpha and a segment of <= 8 nodes of the parent cone that fall in it, the values of 8
+// densities are the dense product
+//     V[density][node] = sum_k C_alpha,density[k] W[k][node],  W[k][node] = T_a(t_s) T_b(t_theta) T_c(t_phi),
+// one m16n8k8 tile per k-step in 3xTF32: A rows are re (row g) and im (row g + 8) of density g,
+// K slot (k-step kk, column j) holds coefficient (r, c) with c = kk / 2, r = 8 (kk % 2) + j
+// (r = 5a + b < 15; slot r = 15 is zero), and the 8 columns are the segment's nodes. Warp w
+// owns densities 8w..8w+7 of the block for every node, so it accumulates the ratio-weighted
+// products of all children into shared memory in a fixed order; its A fragments stay in
+// registers for all segments of one child cone.
+template <int NT>
+__global__ void __launch_bounds__(16 * NT)
+k_prop_mma_tab(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
+               const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
+               const int32_t* __restrict__ slot, int C, const float4* __restrict__ tab_t,
+               const float2* __restrict__ tab_r, const int32_t* __restrict__ tab_k,
+               const int32_t* __restrict__ tab_list, const int16_t* __restrict__ tab_perm,
+               const int32_t* __restrict__ tab_seg, const int32_t* __restrict__ tab_run,
+               const float2* __restrict__ cchild, float2* __restrict__ cparent, const float* __restrict__ W,
+               int cstride, int nrhs, int* __restrict__ status) {
+    constexpr int PS = 3, PT = 5, PP = 5, P = 75;
+    constexpr int NR = 4 * NT;         // densities of the block
+    constexpr int NTHR = 16 * NT;      // NR / 8 warps
+    static_assert(NR % 8 == 0, "a warp owns 8 densities");
+    __shared__ float2 f[NR][P], tmp[NR][P];
+    const int64_t pc = blockIdx.x;
+    const int rhs0 = blockIdx.y * NR;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    for (int x = tid; x < NR * P; x += NTHR) f[x / P][x % P] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int jb = pcone_box[pc];
+    const int g8 = cone_gidx[pc] * 8;
+    const int4 kj = kp[jb];
+    const int dens = rhs0 + 8 * warp + g;  // density of A rows g / g + 8
+    const int dl = 8 * warp + g;           // its row in f
+    for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
+        const int4 kk4 = kd[kb];
+        const int row = g8 + ((kk4.x - 2 * kj.x) | ((kk4.y - 2 * kj.y) << 1) | ((kk4.z - 2 * kj.z) << 2));
+        const int64_t rowP = (int64_t)row * P;
+        const int K = __ldg(&tab_k[row]);
+        for (int kl = 0; kl < K; ++kl) {
+            const int alpha = __ldg(&tab_list[(int64_t)row * kTabList + kl]);
+            const int sl = __ldg(&slot[(int64_t)kb * C + alpha]);
+            if (sl < 0) set_status(status, IFGF_ERR_INTERNAL);
+            const float2* blk = (sl >= 0 && dens < nrhs) ? cchild + ((int64_t)sl * nrhs + dens) * cstride : nullptr;
+            uint32_t ah[10][4], al[10][4];
+#pragma unroll
+            for (int kk = 0; kk < 10; ++kk) {
+                const int c = kk >> 1, r0 = 8 * (kk & 1) + t, r1 = r0 + 4;
+                float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+                if (blk) {
+                    v0 = __ldg(blk + r0 * PP + c);
+                    if (r1 < PS * PT) v1 = __ldg(blk + r1 * PP + c);
+                }
+                tf32_split(v0.x, ah[kk][0], al[kk][0]);
+                tf32_split(v0.y, ah[kk][1], al[kk][1]);
+                tf32_split(v1.x, ah[kk][2], al[kk][2]);
+                tf32_split(v1.y, ah[kk][3], al[kk][3]);
+            }
+            const int sg0 = __ldg(&tab_run[(int64_t)row * (kTabList + 1) + kl]);
+            const int sg1 = __ldg(&tab_run[(int64_t)row * (kTabList + 1) + kl + 1]);
+            // segment descriptor and node coordinates one segment ahead of the contraction
+            int pk = sg0 < sg1 ? __ldg(&tab_seg[rowP + sg0]) : 0;
+            float4 t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < ((pk >> 8) & 0xff)) t4 = __ldg(&tab_t[rowP + (pk & 0xff) + g]);
+            for (int sg = sg0; sg < sg1; ++sg) {
+                const int pk_next = sg + 1 < sg1 ? __ldg(&tab_seg[rowP + sg + 1]) : 0;
+                const int64_t e0 = rowP + (pk & 0xff);
+                const int len = (pk >> 8) & 0xff;
+                // weights of node g of the segment: U[q] = T_a(t_s) T_b(t_theta) for r = t + 4q
+                float Uq[4] = {0.f, 0.f, 0.f, 0.f}, Tp[PP];
+#pragma unroll
+                for (int c = 0; c < PP; ++c) Tp[c] = 0.f;
+                if (g < len) {
+                    float Ts[PS], Tt[PT];
+                    cheb_T<PS>(t4.x, Ts);
+                    cheb_T<PT>(t4.y, Tt);
+                    cheb_T<PP>(t4.z, Tp);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int rr = t + 4 * q, a = rr / PT;
+                        Uq[q] = rr < PS * PT ? pick<PS>(Ts, a) * pick<PT>(Tt, rr - a * PT) : 0.f;
+                    }
+                }
+                // two accumulator chains (even / odd k-steps) to overlap the MMA latency
+                float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+                for (int kk = 0; kk < 10; ++kk) {
+                    const int c = kk >> 1, h = kk & 1;
+                    uint32_t bh[2], bl[2];
+                    tf32_split(Uq[2 * h] * Tp[c], bh[0], bl[0]);
+                    tf32_split(Uq[2 * h + 1] * Tp[c], bh[1], bl[1]);
+                    mma_3xtf32(acc[h], ah[kk], al[kk], bh, bl);
+                }
+                t4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < ((pk_next >> 8) & 0xff)) t4 = __ldg(&tab_t[rowP + (pk_next & 0xff) + g]);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {  // (density g; nodes 2t, 2t+1 of the segment)
+                    const int q = 2 * t + e;
+                    if (q < len) {
+                        const float2 v = cmul(make_float2(acc[0][e] + acc[1][e], acc[0][2 + e] + acc[1][2 + e]),
+                                              __ldg(&tab_r[e0 + q]));
+                        float2& dst = f[dl][__ldg(&tab_perm[e0 + q])];
+                        dst.x += v.x;
+                        dst.y += v.y;
+                    }
+                }
+                pk = pk_next;
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+    // Chebyshev coefficients of every density's node values (phi, theta, s passes)
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int x = tid; x < NR * P; x += NTHR) {
+        const int rl = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+        const float2* rw = &f[rl][(qa * PT + qb) * PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const float w = Wp[qc * PP + k];
+            a.x = fmaf(w, rw[k].x, a.x);
+            a.y = fmaf(w, rw[k].y, a.y);
+        }
+        tmp[rl][n] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < NR * P; x += NTHR) {
+        const int rl = x / P, n = x - (x / P) * P;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < PT; ++jj) {
+            const float w = Wt[qb * PT + jj];
+            const float2 v = tmp[rl][(qa * PT + jj) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        f[rl][n] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < NR * P; x += NTHR) {
+        const int rl = x / P, n = x - (x / P) * P;
+        if (rhs0 + rl >= nrhs) continue;
+        const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const float w = Ws[qa * PS + i];
+            const float2 v = f[rl][(i * PT + qb) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        cparent[(pc * nrhs + rhs0 + rl) * cstride + n] = a;
+    }
+}
+
 // Interpolation with many densities: one warp per chunk of <= 16 targets of one level-d box (the
 // chunks are built by the plan); for every cousin box, an MMA block per distinct cone.
 template <int PS, int PT, int PP, int NT>
@@ -1177,7 +1338,13 @@ void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStre
         }
         if (d == 3) break;
         Level& Lp = p.L[d - 1];
-        if (Lp.nc > 0) {
+        if (Lp.nc > 0 && Lp.n_gam > 0) {
+            TimedScope ts_(TK_PROP, s);
+            IFGF_LAUNCH(k_prop_mma_tab<NT>, dim3((unsigned)Lp.nc, rb), 16 * NT, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gidx,
+                        Lp.k, Lp.cstart, L.k, L.slot, L.g.C, Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm,
+                        Lp.tab_seg, Lp.tab_run, (const float2*)p.coef[cur], (float2*)p.coef[1 - cur], p.Wf,
+                        p.cstride, nrhs, p.d_status);
+        } else if (Lp.nc > 0) {
             TimedScope ts_(TK_PROP, s);
             IFGF_LAUNCH((k_prop_mma<PS, PT, PP, NT>), dim3((unsigned)Lp.nc, rb), 32 * ((P + kChunk - 1) / kChunk), 0, s,
                         Lp.nc, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, Lp.g, L.k, L.slot, L.g,

@@ -91,6 +91,7 @@ struct Level {
     // first entry | length << 8 | list position << 16.
     int32_t* tab_nseg = nullptr;   // [n_gam*8]
     int32_t* tab_seg = nullptr;    // [n_gam*8*P]
+    int32_t* tab_run = nullptr;    // [n_gam*8][kTabList+1] first segment of each child cone, then nseg
     // Target chunks of <= 16 points of one box (tensor-core interpolation with many densities).
     int64_t nchunk = 0;
     int32_t* chunk_box = nullptr;
@@ -591,15 +592,14 @@ __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0,
 //   A (16x8):  a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
 //   B (8x8):   b0 (t, g), b1 (t+4, g)
 //   C (16x8):  c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-// x = hi + lo with both parts representable in TF32 (the split of 3xTF32 products)
+// x = hi + lo for 3xTF32 products: hi keeps the sign, exponent and 10 leading mantissa bits of
+// x rounded to nearest (ties away from zero: add half an ulp of the 10-bit mantissa to the
+// magnitude bits, then clear the 13 low bits), so |lo| <= 2^-11 |x| and lo = x - hi is exact in
+// FP32. The tensor core reads the 10 leading mantissa bits of lo, which leaves a relative
+// error below 2^-21 |x| in hi + lo.
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
-    hi = tf32_bits(x);
-    lo = tf32_bits(x - __uint_as_float(hi));
+    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm volatile(

@@ -343,7 +343,8 @@ __global__ void k_node_tables(int64_t total, const int32_t* __restrict__ gam_lis
 __global__ void k_node_lists(int P, float4* __restrict__ tab_t, float2* __restrict__ tab_r,
                              int32_t* __restrict__ tab_k, int32_t* __restrict__ tab_list,
                              int16_t* __restrict__ tab_perm, int32_t* __restrict__ tab_nseg,
-                             int32_t* __restrict__ tab_seg, int* __restrict__ overflow) {
+                             int32_t* __restrict__ tab_seg, int32_t* __restrict__ tab_run,
+                             int* __restrict__ overflow) {
     __shared__ int alpha[128];  // child cone of each node
     __shared__ int first[128];  // 1 if the node is the first with its child cone
     __shared__ int idx[128];    // list position, defined where first[] is set
@@ -408,10 +409,18 @@ __global__ void k_node_lists(int P, float4* __restrict__ tab_t, float2* __restri
             const int len = min(kSegLen, before + cnt - pos);
             tab_seg[row * P + sidx] = pos | (len << 8) | (k << 16);
         }
+        if (first[n] && k < kTabList) {  // first segment of this child cone's run
+            int rs = 0;
+            for (int j = 0; j < before; ++j) rs += segst[j];
+            tab_run[row * (kTabList + 1) + k] = rs;
+        }
         if (n == 0) {
             int ns = 0;
             for (int j = 0; j < P; ++j) ns += segst[j];
             tab_nseg[row] = ns;
+            int K = 0;
+            for (int m = 0; m < P; ++m) K += first[m];
+            tab_run[row * (kTabList + 1) + min(K, kTabList)] = ns;
         }
     }
 }
@@ -614,10 +623,11 @@ void build_node_tables(Plan& p, int dp) {
         Lp.tab_perm = dalloc<int16_t>(p, (size_t)entries);
         Lp.tab_nseg = dalloc<int32_t>(p, (size_t)n_gam * 8);
         Lp.tab_seg = dalloc<int32_t>(p, (size_t)entries);
+        Lp.tab_run = dalloc<int32_t>(p, (size_t)n_gam * 8 * (kTabList + 1));
         int* ovf = dalloc<int>(p, 1);
         IFGF_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), p.stream));
         IFGF_LAUNCH(k_node_lists, (unsigned)(n_gam * 8), 128, 0, p.stream, p.P, Lp.tab_t, Lp.tab_r, Lp.tab_k,
-                    Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, ovf);
+                    Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, Lp.tab_run, ovf);
         const int overflow = read_one(p, ovf);
         dfree_ptr(p, ovf);
         if (overflow) {  // some row has more distinct child cones than a list holds: no tables
@@ -630,6 +640,7 @@ void build_node_tables(Plan& p, int dp) {
             dfree_ptr(p, Lp.tab_perm);
             dfree_ptr(p, Lp.tab_nseg);
             dfree_ptr(p, Lp.tab_seg);
+            dfree_ptr(p, Lp.tab_run);
             Lp.n_gam = 0;
         }
     }
