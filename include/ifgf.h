@@ -52,14 +52,18 @@ typedef enum {
  * Method parameters.  Defaults (ifgf_options_default): MIXED, base cone grid (2, 4, 8),
  * tau = 0.5, leaf_target = 64, max_nrhs = 1.
  *   base_cones  (n_s, n_theta, n_phi) of the cone grid of boxes of at most tau wavelengths;
- *               the grid of a level whose box side H_d exceeds tau*2^(e-1) wavelengths is the
- *               base grid doubled e times in all three directions (n_phi >= 4, even).
+ *               level d uses the base grid doubled e times in all three directions, e the
+ *               smallest integer with kappa H_d <= 2 pi tau 2^e (1 + 2^-10) (n_phi >= 4, even).
  *   leaf_target when levels == 0, D is the smallest level >= 3 whose mean relevant-leaf
  *               occupancy N / n_D is at most leaf_target.
  *   max_nrhs    largest nrhs that ifgf_apply will accept (buffers are sized for it).
  *   rhs_block   the coefficient buffers hold this many densities; ifgf_apply sweeps the levels
  *               once per block of densities (0: the largest block, up to max_nrhs, whose two
  *               coefficient buffers fit in half the free device memory at plan time).
+ *   cone_table  how a level finds the relevant cone of (box, cone index): 0 automatic (a dense
+ *               n_d x C_d table while it has fewer than 2^31 entries, else the sorted cone list
+ *               searched per box), 1 always dense (IFGF_ERR_UNSUPPORTED beyond 2^31 entries),
+ *               2 always the sorted list.  Results do not depend on the choice.
  */
 typedef struct {
     int32_t struct_size;   /* sizeof(ifgf_options) */
@@ -69,6 +73,8 @@ typedef struct {
     int32_t max_nrhs;
     int32_t rhs_block;     /* densities per level sweep; 0 = as many as fit half the free memory */
     double tau;
+    int32_t cone_table;    /* 0 automatic, 1 dense, 2 sorted list */
+    int32_t reserved;      /* must be 0 */
 } ifgf_options;
 
 void ifgf_options_default(ifgf_options* opt);

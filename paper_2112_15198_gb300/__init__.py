@@ -50,6 +50,8 @@ class Options(ctypes.Structure):
         ("max_nrhs", ctypes.c_int32),
         ("rhs_block", ctypes.c_int32),
         ("tau", ctypes.c_double),
+        ("cone_table", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -169,7 +171,7 @@ class Plan:
 
     def __init__(self, points, kappa: float, orders=(3, 5, 5), levels: int = 0, precision: str = "mixed",
                  base_cones=(2, 4, 8), tau: float = 0.5, leaf_target: int = 64, max_nrhs: int = 1, stream=None,
-                 n: int | None = None, rhs_block: int = 0):
+                 n: int | None = None, rhs_block: int = 0, cone_table: str = "auto"):
         lib = load()
         self._lib = lib
         opt = Options()
@@ -180,6 +182,7 @@ class Plan:
         opt.leaf_target = int(leaf_target)
         opt.max_nrhs = int(max_nrhs)
         opt.rhs_block = int(rhs_block)
+        opt.cone_table = {"auto": 0, "dense": 1, "sorted": 2}[cone_table]
         if n is None:
             shape = tuple(points.shape)
             if len(shape) != 2 or shape[0] != 3:

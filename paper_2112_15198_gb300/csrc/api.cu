@@ -163,6 +163,8 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
     else if (opt.leaf_target < 1) why = "leaf_target must be >= 1";
     else if (opt.max_nrhs < 1 || opt.max_nrhs > 65535) why = "max_nrhs out of range";
     else if (opt.rhs_block < 0) why = "rhs_block must be >= 0";
+    else if (opt.cone_table < 0 || opt.cone_table > 2) why = "cone_table must be 0, 1 or 2";
+    else if (opt.reserved != 0) why = "reserved must be 0";
     else if (!(opt.tau > 0.0) || !std::isfinite(opt.tau)) why = "tau must be finite and > 0";
     else if (!((Ps == 3 && Pt == 5 && Pp == 5) || (Ps == 5 && Pt == 7 && Pp == 7)))
         why = "orders must be (3,5,5) or (5,7,7) in this build";
@@ -204,24 +206,30 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
         IFGF_CUDA(cudaMemcpyAsync(p->Wd, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, p->stream));
         IFGF_CUDA(cudaMemcpyAsync(p->Wf, Wf.data(), sizeof(float) * Wf.size(), cudaMemcpyHostToDevice, p->stream));
         const size_t csz = p->precision == IFGF_PREC_MIXED ? sizeof(float2) : sizeof(double2);
-        int64_t cmax = 1;
-        for (int d = 3; d <= p->D; ++d) cmax = std::max<int64_t>(cmax, p->L[d].nc);
-        p->coef_cap = cmax;
-        // Coefficient buffers for a block of densities that fits half of the free device memory
-        // (a multiple of 4 when blocked); ifgf_apply sweeps the levels once per block.
+        // Coefficient arena for a block of densities: half of the free device memory when that
+        // holds it, else up to 90% (minus the density and output buffers); ifgf_apply sweeps the
+        // levels once per block (a multiple of 4 densities when blocked).
         {
             size_t free_b = 0, total_b = 0;
             IFGF_CUDA(cudaMemGetInfo(&free_b, &total_b));
-            const size_t per_rhs = 2 * (size_t)cmax * p->cstride * csz;
-            const size_t fit = std::max<size_t>(1, (free_b / 2) / std::max<size_t>(per_rhs, 1));
+            const size_t io = 2 * (size_t)N * p->max_nrhs * csz + ((size_t)1 << 28);
+            const size_t usable = free_b > io ? free_b - io : 0;
+            int64_t M = layout_arena(*p, usable / 2);
+            size_t budget = usable / 2;
+            if (M == 0) {
+                budget = usable / 10 * 9;
+                M = layout_arena(*p, budget);
+            }
+            if (M == 0) fail(IFGF_ERR_OOM, "the coefficient arena of one density does not fit in device memory");
+            p->arena_cones = M;
+            const size_t per_rhs = (size_t)M * p->cstride * csz;
+            const size_t fit = std::max<size_t>(1, budget / std::max<size_t>(per_rhs, 1));
             int blk = (int)std::min<size_t>((size_t)p->max_nrhs, fit);
             if (blk < p->max_nrhs && blk >= 8) blk &= ~3;
             if (opt.rhs_block > 0) blk = std::min(opt.rhs_block, p->max_nrhs);
             p->rhs_block = std::max(1, blk);
         }
-        const size_t cbytes = (size_t)cmax * p->rhs_block * p->cstride * csz;
-        p->coef[0] = dalloc<char>(*p, cbytes);
-        p->coef[1] = dalloc<char>(*p, cbytes);
+        p->arena = dalloc<char>(*p, (size_t)p->arena_cones * p->rhs_block * p->cstride * csz);
         p->a_s = dalloc<char>(*p, (size_t)N * p->max_nrhs * csz);
         p->I_s = dalloc<char>(*p, (size_t)N * p->max_nrhs * csz);
         p->d_status = dalloc<int>(*p, 1);

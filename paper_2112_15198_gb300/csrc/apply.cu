@@ -263,7 +263,7 @@ template <int PS, int PT, int PP>
 __global__ void __launch_bounds__(kPropThreads, 5)
 k_prop_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
            const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
-           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
+           const int4* __restrict__ kd, ConeMap cm, LevelGrid g,
            const float2* __restrict__ cchild, float2* __restrict__ cparent, int sh, float ku,
            const float* __restrict__ W, int cstride, int nrhs, int* __restrict__ status) {
     constexpr int P = PS * PT * PP;
@@ -325,7 +325,7 @@ k_prop_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __
         const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
         const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
         const ConeLocal cl = locate_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
-        const int s = __ldg(&slot[(int64_t)kb * g.C + cl.gamma(g)]);
+        const int s = cm.find(kb, cl.gamma(g));
         float2 t = make_float2(0.f, 0.f);
         if (s < 0) {
             set_status(status, IFGF_ERR_INTERNAL);
@@ -412,7 +412,7 @@ template <int PS, int PT, int PP>
 __global__ void __launch_bounds__(kSegThreads, 3)
 k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
                const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
-               const int32_t* __restrict__ slot, int C, const float4* __restrict__ tab_t,
+               ConeMap cm, const float4* __restrict__ tab_t,
                const float2* __restrict__ tab_r, const int32_t* __restrict__ tab_k,
                const int32_t* __restrict__ tab_list, const int16_t* __restrict__ tab_perm,
                const int32_t* __restrict__ tab_nseg, const int32_t* __restrict__ tab_seg,
@@ -465,7 +465,7 @@ k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
         if (ch >= s_nch[c]) continue;
         const int row = s_row[c][ch];
         if (k >= __ldg(&tab_k[row])) continue;
-        const int sl = __ldg(&slot[(int64_t)(s_kb0[c] + ch) * C + __ldg(&tab_list[(int64_t)row * kTabList + k])]);
+        const int sl = cm.find(s_kb0[c] + ch, __ldg(&tab_list[(int64_t)row * kTabList + k]));
         s_slot[c][ch][k] = sl;
         if (sl >= 0) {
             const char* blk = reinterpret_cast<const char*>(cchild + ((int64_t)sl * nrhs + r) * cstride);
@@ -570,7 +570,7 @@ k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
 template <int PS, int PT, int PP>
 __global__ void k_prop_f64(const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
                            const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
-                           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
+                           const int4* __restrict__ kd, ConeMap cm, LevelGrid g,
                            const double2* __restrict__ cchild, double2* __restrict__ cparent, int sh, double kappa,
                            double a0, double a1, double a2, double Hd, const double* __restrict__ W, int cstride,
                            int nrhs, int* __restrict__ status) {
@@ -599,7 +599,7 @@ __global__ void k_prop_f64(const int32_t* __restrict__ pcone_box, const int32_t*
             const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
             const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
             const int gam = classify_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
-            const int sl = slot[(int64_t)kb * g.C + gam];
+            const int sl = cm.find(kb, gam);
             if (sl < 0) {
                 set_status(status, IFGF_ERR_INTERNAL);
                 continue;
@@ -631,7 +631,7 @@ template <int PS, int PT, int PP>
 __global__ void k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
                              const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
                              const int32_t* __restrict__ cs, const float4* __restrict__ off,
-                             const int32_t* __restrict__ slot, LevelGrid g, const float2* __restrict__ coef,
+                             ConeMap cm, LevelGrid g, const float2* __restrict__ coef,
                              const float* __restrict__ phtab, float ku, float inv4piu, float2* __restrict__ Is,
                              int cstride, int nrhs, int* __restrict__ status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -655,7 +655,7 @@ __global__ void k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
         const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
         const ConeLocal cl = locate_f32(g, vx, vy, vz);
-        const int s = __ldg(&slot[(int64_t)B * g.C + cl.gamma(g)]);
+        const int s = cm.find(B, cl.gamma(g));
         if (s < 0) {
             set_status(status, IFGF_ERR_INTERNAL);
             continue;
@@ -682,7 +682,7 @@ template <int PS, int PT, int PP>
 __global__ void k_interp_f64(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
                              const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
                              const int32_t* __restrict__ cs, const float4* __restrict__ off,
-                             const double* __restrict__ Xs, const int32_t* __restrict__ slot, LevelGrid g,
+                             const double* __restrict__ Xs, ConeMap cm, LevelGrid g,
                              const double2* __restrict__ coef, double kappa, double a0, double a1, double a2,
                              double Hd, double2* __restrict__ Is, int cstride, int nrhs, int* __restrict__ status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -701,7 +701,7 @@ __global__ void k_interp_f64(int64_t N, int sh, const int32_t* __restrict__ pbox
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
         const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
         const int gam = classify_f32(g, vx, vy, vz);
-        const int s = slot[(int64_t)B * g.C + gam];
+        const int s = cm.find(B, gam);
         if (s < 0) {
             set_status(status, IFGF_ERR_INTERNAL);
             continue;
@@ -750,7 +750,7 @@ template <int PS, int PT, int PP, int NT>
 __global__ void __launch_bounds__(32 * ((PS * PT * PP + kChunk - 1) / kChunk))
 k_prop_mma(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
            const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
-           const int4* __restrict__ kd, const int32_t* __restrict__ slot, LevelGrid g,
+           const int4* __restrict__ kd, ConeMap cm, LevelGrid g,
            const float2* __restrict__ cchild, float2* __restrict__ cparent, int sh, float ku,
            const float* __restrict__ W, int cstride, int nrhs, int* __restrict__ status) {
     constexpr int P = PS * PT * PP;
@@ -803,7 +803,7 @@ k_prop_mma(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __
         cheb_T<PT>(c1.tt, Tt1);
         cheb_T<PP>(c1.tp, Tp1);
         for_each_cone(c0.gamma(g), c1.gamma(g), v0, v1, [&](int alpha, bool m0, bool m1) {
-            const int s = __ldg(&slot[(int64_t)kb * g.C + alpha]);
+            const int s = cm.find(kb, alpha);
             if (s < 0) {
                 if (m0 || m1) set_status(status, IFGF_ERR_INTERNAL);
                 return;
@@ -894,7 +894,7 @@ template <int NT>
 __global__ void __launch_bounds__(16 * NT)
 k_prop_mma_tab(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
                const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
-               const int32_t* __restrict__ slot, int C, const float4* __restrict__ tab_t,
+               ConeMap cm, const float4* __restrict__ tab_t,
                const float2* __restrict__ tab_r, const int32_t* __restrict__ tab_k,
                const int32_t* __restrict__ tab_list, const int16_t* __restrict__ tab_perm,
                const int32_t* __restrict__ tab_seg, const int32_t* __restrict__ tab_run,
@@ -922,7 +922,7 @@ k_prop_mma_tab(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
         const int K = __ldg(&tab_k[row]);
         for (int kl = 0; kl < K; ++kl) {
             const int alpha = __ldg(&tab_list[(int64_t)row * kTabList + kl]);
-            const int sl = __ldg(&slot[(int64_t)kb * C + alpha]);
+            const int sl = cm.find(kb, alpha);
             if (sl < 0) set_status(status, IFGF_ERR_INTERNAL);
             const float2* blk = (sl >= 0 && dens < nrhs) ? cchild + ((int64_t)sl * nrhs + dens) * cstride : nullptr;
             uint32_t ah[10][4], al[10][4];
@@ -1048,7 +1048,7 @@ __global__ void __launch_bounds__(128)
 k_interp_mma(int64_t nchunk, const int32_t* __restrict__ chunk_box, const int32_t* __restrict__ chunk_start,
              const int32_t* __restrict__ start_d, int64_t N, int sh, const int32_t* __restrict__ pbox_D,
              const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
-             const int32_t* __restrict__ cs, const float4* __restrict__ off, const int32_t* __restrict__ slot,
+             const int32_t* __restrict__ cs, const float4* __restrict__ off, ConeMap cm,
              LevelGrid g, const float2* __restrict__ coef, const float* __restrict__ phtab, float ku, float inv4piu,
              float2* __restrict__ Is, int cstride, int nrhs, int* __restrict__ status) {
     const int64_t ch = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -1114,7 +1114,7 @@ k_interp_mma(int64_t nchunk, const int32_t* __restrict__ chunk_box, const int32_
         cheb_T<PT>(c1.tt, Tt1);
         cheb_T<PP>(c1.tp, Tp1);
         for_each_cone(c0.gamma(g), c1.gamma(g), v0, v1, [&](int alpha, bool m0, bool m1) {
-            const int s = __ldg(&slot[(int64_t)B * g.C + alpha]);
+            const int s = cm.find(B, alpha);
             if (s < 0) {
                 if (m0 || m1) set_status(status, IFGF_ERR_INTERNAL);
                 return;
@@ -1292,6 +1292,20 @@ __global__ void k_leaf_f32_multi(const int32_t* __restrict__ cone_box, const int
 // ---- driver -------------------------------------------------------------------------------
 // Mixed precision with many densities: tensor-core propagation and interpolation, density-
 // blocked near field and leaf evaluation.
+// Propagation into level d-1, slice by slice in the order the coefficient arena requires (the
+// parents are written at the other end of the arena from the children being read): launch(lo, n)
+// runs the parent cones [lo, lo + n).
+template <class F>
+void for_each_slice(const Plan& p, int d, F&& launch) {
+    const std::vector<int64_t>& b = p.L[d - 1].pslice;
+    const int ks = (int)b.size() - 1;
+    const bool child_at_start = (p.D - d) % 2 == 0;
+    for (int j = 0; j < ks; ++j) {
+        const int i = child_at_start ? ks - 1 - j : j;
+        if (b[i + 1] > b[i]) launch(b[i], b[i + 1] - b[i]);
+    }
+}
+
 template <int NT, int PS, int PT, int PP>
 void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
     constexpr int P = PS * PT * PP;
@@ -1309,7 +1323,6 @@ void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStre
     const dim3 gN(grid_for(N, kThreads), nrhs);
     const unsigned rb = (unsigned)((nrhs + NR - 1) / NR);
     const unsigned rb8 = (unsigned)((nrhs + NRB - 1) / NRB);
-    int cur = 0;
     {
         TimedScope ts_(TK_PERM, s);
         IFGF_LAUNCH(k_perm_in<float2>, gN, kThreads, 0, s, (const float2*)dens, p.perm, N, as);
@@ -1325,7 +1338,7 @@ void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStre
         TimedScope ts_(TK_LEAF, s);
         IFGF_LAUNCH((k_leaf_f32_multi<PS, PT, PP, NRB>), dim3((unsigned)LD.nc, rb8), BT, 0, s, LD.cone_box,
                     LD.cone_gam, LD.g, LD.start, p.off, as, N, (float)(p.kappa * LD.g.h64), 1.0f / LD.g.hg, p.Wf,
-                    (float2*)p.coef[cur], p.cstride, nrhs);
+                    (float2*)level_coef(p, D, nrhs), p.cstride, nrhs);
     }
     for (int d = D; d >= 3; --d) {
         Level& L = p.L[d];
@@ -1333,25 +1346,29 @@ void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStre
         if (((mask >> d) & 1) && L.nchunk > 0) {
             TimedScope ts_(TK_INTERP, s);
             IFGF_LAUNCH((k_interp_mma<PS, PT, PP, NT>), dim3((unsigned)((L.nchunk + 3) / 4), rb), 128, 0, s, L.nchunk,
-                        L.chunk_box, L.chunk_start, L.start, N, sh, LD.pbox, LD.k, L.k, L.ncs, L.cs, p.off, L.slot, L.g,
-                        (const float2*)p.coef[cur], L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status);
+                        L.chunk_box, L.chunk_start, L.start, N, sh, LD.pbox, LD.k, L.k, L.ncs, L.cs, p.off, L.cmap(), L.g,
+                        (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status);
         }
         if (d == 3) break;
         Level& Lp = p.L[d - 1];
+        const float2* cc = (const float2*)level_coef(p, d, nrhs);
+        float2* cp = (float2*)level_coef(p, d - 1, nrhs);
+        const int64_t cone = (int64_t)nrhs * p.cstride;
         if (Lp.nc > 0 && Lp.n_gam > 0) {
             TimedScope ts_(TK_PROP, s);
-            IFGF_LAUNCH(k_prop_mma_tab<NT>, dim3((unsigned)Lp.nc, rb), 16 * NT, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gidx,
-                        Lp.k, Lp.cstart, L.k, L.slot, L.g.C, Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm,
-                        Lp.tab_seg, Lp.tab_run, (const float2*)p.coef[cur], (float2*)p.coef[1 - cur], p.Wf,
-                        p.cstride, nrhs, p.d_status);
+            for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                IFGF_LAUNCH(k_prop_mma_tab<NT>, dim3((unsigned)n, rb), 16 * NT, 0, s, n, Lp.cone_box + lo,
+                            Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list,
+                            Lp.tab_perm, Lp.tab_seg, Lp.tab_run, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
+            });
         } else if (Lp.nc > 0) {
             TimedScope ts_(TK_PROP, s);
-            IFGF_LAUNCH((k_prop_mma<PS, PT, PP, NT>), dim3((unsigned)Lp.nc, rb), 32 * ((P + kChunk - 1) / kChunk), 0, s,
-                        Lp.nc, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, Lp.g, L.k, L.slot, L.g,
-                        (const float2*)p.coef[cur], (float2*)p.coef[1 - cur], sh, ku, p.Wf, p.cstride, nrhs,
-                        p.d_status);
+            for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                IFGF_LAUNCH((k_prop_mma<PS, PT, PP, NT>), dim3((unsigned)n, rb), 32 * ((P + kChunk - 1) / kChunk), 0, s,
+                            n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(), L.g, cc,
+                            cp + lo * cone, sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
+            });
         }
-        cur = 1 - cur;
     }
     {
         TimedScope ts_(TK_PERM, s);
@@ -1384,7 +1401,6 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
     const double u = p.u;
     const double HD = std::ldexp(p.H1, 1 - D);
     Level& LD = p.L[D];
-    int cur = 0;
     if (mixed && nrhs >= kMmaMinRhs && PS == 3 && PT == 5 && PP == 5) {
         run_apply_multi<PS, PT, PP>(p, dens, nrhs, out, s, near, mask);
     } else if (mixed) {
@@ -1409,8 +1425,8 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
             {
                 TimedScope ts_(TK_LEAF, s);
                 IFGF_LAUNCH((k_leaf_f32<PS, PT, PP>), dim3((unsigned)LD.nc, nrhs), BT, 0, s, LD.cone_box, LD.cone_gam,
-                            LD.g, LD.start, p.off, as, N, kh, 1.0f / LD.g.hg, p.Wf, (float2*)p.coef[cur], p.cstride,
-                            nrhs);
+                            LD.g, LD.start, p.off, as, N, kh, 1.0f / LD.g.hg, p.Wf, (float2*)level_coef(p, D, nrhs),
+                            p.cstride, nrhs);
             }
         for (int d = D; d >= 3; --d) {
             Level& L = p.L[d];
@@ -1419,29 +1435,32 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                 {
                     TimedScope ts_(TK_INTERP, s);
                     IFGF_LAUNCH((k_interp_f32<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs,
-                                L.cs, p.off, L.slot, L.g, (const float2*)p.coef[cur], L.phtab, ku, inv4piu, Is, p.cstride,
-                                nrhs, p.d_status);
+                                L.cs, p.off, L.cmap(), L.g, (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu,
+                                Is, p.cstride, nrhs, p.d_status);
                 }
             if (d == 3) break;
             Level& Lp = p.L[d - 1];
+            const float2* cc = (const float2*)level_coef(p, d, nrhs);
+            float2* cp = (float2*)level_coef(p, d - 1, nrhs);
+            const int64_t cone = (int64_t)nrhs * p.cstride;
             if (Lp.nc > 0 && Lp.n_gam > 0 && PS * PT * PP <= 75) {  // tables are built for (3,5,5) only
                 TimedScope ts_(TK_PROP, s);
                 constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
                               TP = PS * PT * PP <= 75 ? PP : 5;
-                IFGF_LAUNCH((k_prop_tab_f32<TS, TT, TP>), dim3((unsigned)((Lp.nc + kSegCones - 1) / kSegCones), nrhs),
-                            kSegThreads, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, L.slot, L.g.C,
-                            Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg,
-                            (const float2*)p.coef[cur],
-                            (float2*)p.coef[1 - cur], p.Wf, p.cstride, nrhs, p.d_status);
-            } else if (Lp.nc > 0)
-                {
-                    TimedScope ts_(TK_PROP, s);
-                    IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((Lp.nc + kPropCones - 1) / kPropCones), nrhs),
-                                kPropThreads, 0, s, Lp.nc, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, Lp.g, L.k, L.slot,
-                                L.g, (const float2*)p.coef[cur], (float2*)p.coef[1 - cur], sh, ku, p.Wf, p.cstride,
-                                nrhs, p.d_status);
-                }
-            cur = 1 - cur;
+                for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                    IFGF_LAUNCH((k_prop_tab_f32<TS, TT, TP>), dim3((unsigned)((n + kSegCones - 1) / kSegCones), nrhs),
+                                kSegThreads, 0, s, n, Lp.cone_box + lo, Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k,
+                                L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, Lp.tab_nseg,
+                                Lp.tab_seg, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
+                });
+            } else if (Lp.nc > 0) {
+                TimedScope ts_(TK_PROP, s);
+                for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                    IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((n + kPropCones - 1) / kPropCones), nrhs),
+                                kPropThreads, 0, s, n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k,
+                                L.cmap(), L.g, cc, cp + lo * cone, sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
+                });
+            }
         }
         {
             TimedScope ts_(TK_PERM, s);
@@ -1466,7 +1485,7 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                 TimedScope ts_(TK_LEAF, s);
                 IFGF_LAUNCH((k_leaf_f64<PS, PT, PP>), dim3((unsigned)LD.nc, nrhs), BT, 0, s, LD.cone_box, LD.cone_gam,
                             LD.g, LD.start, LD.k, p.Xs, as, N, p.kappa, p.a[0], p.a[1], p.a[2], HD, p.Wd,
-                            (double2*)p.coef[cur], p.cstride, nrhs);
+                            (double2*)level_coef(p, D, nrhs), p.cstride, nrhs);
             }
         for (int d = D; d >= 3; --d) {
             Level& L = p.L[d];
@@ -1476,20 +1495,22 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                 {
                     TimedScope ts_(TK_INTERP, s);
                     IFGF_LAUNCH((k_interp_f64<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs,
-                                L.cs, p.off, p.Xs, L.slot, L.g, (const double2*)p.coef[cur], p.kappa, p.a[0], p.a[1],
+                                L.cs, p.off, p.Xs, L.cmap(), L.g, (const double2*)level_coef(p, d, nrhs), p.kappa, p.a[0], p.a[1],
                                 p.a[2], Hd, Is, p.cstride, nrhs, p.d_status);
                 }
             if (d == 3) break;
             Level& Lp = p.L[d - 1];
-            if (Lp.nc > 0)
-                {
-                    TimedScope ts_(TK_PROP, s);
-                    IFGF_LAUNCH((k_prop_f64<PS, PT, PP>), dim3((unsigned)Lp.nc, nrhs), BT, 0, s, Lp.cone_box, Lp.cone_gam,
-                                Lp.k, Lp.cstart, Lp.g, L.k, L.slot, L.g, (const double2*)p.coef[cur],
-                                (double2*)p.coef[1 - cur], sh, p.kappa, p.a[0], p.a[1], p.a[2], Hd, p.Wd, p.cstride, nrhs,
-                                p.d_status);
-                }
-            cur = 1 - cur;
+            if (Lp.nc > 0) {
+                TimedScope ts_(TK_PROP, s);
+                const double2* cc = (const double2*)level_coef(p, d, nrhs);
+                double2* cp = (double2*)level_coef(p, d - 1, nrhs);
+                const int64_t cone = (int64_t)nrhs * p.cstride;
+                for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                    IFGF_LAUNCH((k_prop_f64<PS, PT, PP>), dim3((unsigned)n, nrhs), BT, 0, s, Lp.cone_box + lo,
+                                Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(), L.g, cc, cp + lo * cone, sh,
+                                p.kappa, p.a[0], p.a[1], p.a[2], Hd, p.Wd, p.cstride, nrhs, p.d_status);
+                });
+            }
         }
         {
             TimedScope ts_(TK_PERM, s);

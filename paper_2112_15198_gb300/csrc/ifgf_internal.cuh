@@ -55,6 +55,28 @@ struct LevelGrid {
     const double* pnode64;     // [np*Pp] phi of nodes
 };
 
+// Cone lookup (box, gamma) -> index of the relevant cone, or -1. Dense levels keep the table
+// slot[box * C + gamma] (one load); levels whose table would be too large keep only the
+// cone list, sorted by (box, gamma), with the first cone of every box (binary search).
+struct ConeMap {
+    const int32_t* slot;  // dense table, or nullptr
+    int32_t C;
+    const int32_t* bcs;   // [n+1] first cone of every box (sparse levels)
+    const int32_t* gam;   // [nc] cone index gamma of every cone (sparse levels)
+    __device__ __forceinline__ int find(int box, int gamma) const {
+        if (slot) return __ldg(&slot[(int64_t)box * C + gamma]);
+        int lo = __ldg(&bcs[box]);
+        const int end = __ldg(&bcs[box + 1]);
+        int hi = end;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&gam[mid]) < gamma) lo = mid + 1;
+            else hi = mid;
+        }
+        return (lo < end && __ldg(&gam[lo]) == gamma) ? lo : -1;
+    }
+};
+
 struct Level {
     int32_t n = 0;                 // relevant boxes R_B^d
     uint64_t* key = nullptr;       // [n] Morton keys, ascending
@@ -69,7 +91,9 @@ struct Level {
     int32_t* cs = nullptr;         // [n*189] ascending
     LevelGrid g{};
     int64_t nc = 0;                // relevant cones R_C^d
-    int32_t* slot = nullptr;       // [n*C] cone index or -1
+    int32_t* slot = nullptr;       // [n*C] cone index or -1 (dense levels; nullptr when sparse)
+    int32_t* bcs = nullptr;        // [n+1] first cone of every box (sparse levels)
+    ConeMap cmap() const { return ConeMap{slot, g.C, bcs, cone_gam}; }
     int32_t* cone_box = nullptr;   // [nc]
     int32_t* cone_gam = nullptr;   // [nc]
     float* phtab = nullptr;        // [28] (kappa H_d sqrt(m)) mod 2 pi, m = |k_A - k_B|^2
@@ -96,6 +120,8 @@ struct Level {
     int64_t nchunk = 0;
     int32_t* chunk_box = nullptr;
     int32_t* chunk_start = nullptr;
+    // Propagation into this level (as the parent level): cone boundaries of its slices.
+    std::vector<int64_t> pslice;
 };
 constexpr int kTabList = 32;
 constexpr int kSegLen = 8;  // nodes of one child cone evaluated by one thread
@@ -122,8 +148,13 @@ struct Plan {
     double* Wd = nullptr;          // same in FP64
     void* a_s = nullptr;           // sorted densities [nrhs][N]
     void* I_s = nullptr;           // sorted output [nrhs][N]
-    void* coef[2] = {nullptr, nullptr};
-    int64_t coef_cap = 0;          // cones per coefficient buffer
+    // Coefficient arena of arena_cones cone blocks (each rhs_block densities x cstride). Level d
+    // lives at the start of the arena when D - d is even and at its end otherwise, so the
+    // propagation into level d-1 writes at the other end while it reads level d; done in slices
+    // of parent cones (Level::pslice), the reads still ahead never meet the writes, and the
+    // arena needs about max_d n_c(d) (1 + 1/slices) cones instead of two full levels.
+    char* arena = nullptr;
+    int64_t arena_cones = 0;
     int* d_status = nullptr;       // sticky device status
     std::vector<void*> allocs;
 };
@@ -202,6 +233,16 @@ void radix_sort_pairs(Plan& p, uint64_t* keys, int32_t* vals, int64_t n, int end
 
 // ---- stages -----------------------------------------------------------------------------
 void build_plan(Plan& p, const double* points, const ifgf_options& opt, int levels);
+// Coefficient arena layout: slices per level and arena size for at most `budget` bytes per
+// density (cone blocks of cstride complex values); returns the arena size in cones, 0 if the
+// levels cannot be laid out in the budget.
+int64_t layout_arena(Plan& p, size_t budget_per_rhs);
+// Level d's first cone block in the arena for blocks of nb densities.
+inline char* level_coef(const Plan& p, int d, int nb) {
+    const size_t csz = p.precision == IFGF_PREC_MIXED ? 8 : 16;
+    const size_t cone = (size_t)nb * p.cstride * csz;
+    return ((p.D - d) % 2 == 0) ? p.arena : p.arena + (size_t)(p.arena_cones - p.L[d].nc) * cone;
+}
 void destroy_plan(Plan& p);
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask);
 

@@ -228,13 +228,46 @@ __global__ void k_cousins(const int4* __restrict__ bk, const int32_t* __restrict
 }
 
 // ---- cone activation (Eq. (4), discrete form) -------------------------------------------
+// A relevant (box, gamma) is recorded either as a flag of the dense n_d x C_d table or as the
+// key box * C + gamma in an open-addressing hash set (sparse levels). In the hash set the lanes
+// of a warp that hold the same key insert it once.
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kMaxProbe = 128;
+struct ConeMark {
+    int32_t* dense;             // [n*C] flags, or nullptr
+    unsigned long long* hkeys;  // [hmask + 1] keys or kEmptyKey
+    unsigned long long hmask;
+    int64_t C;
+    int* overflow;
+    __device__ __forceinline__ void mark(int box, int gamma) const {
+        const unsigned long long key = (unsigned long long)box * (unsigned long long)C + (unsigned long long)gamma;
+        if (dense) {
+            dense[key] = 1;
+            return;
+        }
+        const unsigned same = __match_any_sync(__activemask(), key);
+        if ((int)(threadIdx.x & 31) != __ffs(same) - 1) return;  // one lane per distinct key
+        unsigned long long h = (key * 0x9E3779B97F4A7C15ull) >> 17;
+        for (int probe = 0; probe < kMaxProbe; ++probe, ++h) {
+            h &= hmask;
+            const unsigned long long cur = __ldcg(&hkeys[h]);
+            if (cur == key) return;
+            if (cur == kEmptyKey) {
+                const unsigned long long prev = atomicCAS(&hkeys[h], kEmptyKey, key);
+                if (prev == kEmptyKey || prev == key) return;
+            }
+        }
+        atomicExch(overflow, 1);  // table too full: the level is redone with a larger one
+    }
+};
+
 // Cousin points x in V B: every point marks, in each cousin box of its level-d box, the cone
 // that contains it.
 __global__ void k_mark_cousin_points(int64_t N, int D, int d, const int32_t* __restrict__ pbox_d,
                                      const int32_t* __restrict__ pbox_D, const int4* __restrict__ kD,
                                      const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
                                      const int32_t* __restrict__ cs, const float4* __restrict__ off, LevelGrid g,
-                                     int32_t* __restrict__ mark) {
+                                     ConeMark mark) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int A = pbox_d[i];
@@ -248,7 +281,7 @@ __global__ void k_mark_cousin_points(int64_t N, int D, int d, const int32_t* __r
         const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
         const float vz = __fadd_rn((float)((2 * kl.z + 1) - ((2 * kb.z + 1) << sh)), o.z);
-        mark[(int64_t)B * g.C + classify_f32(g, vx, vy, vz)] = 1;
+        mark.mark(B, classify_f32(g, vx, vy, vz));
     }
 }
 
@@ -267,8 +300,7 @@ __device__ __forceinline__ float3 node_grid(const LevelGrid& gp, int Ps, int Pt,
 __global__ void k_mark_parent_nodes(int64_t ncp, int P, int Ps, int Pt, int Pp, int D, int d,
                                     const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
                                     const int4* __restrict__ kp, const int32_t* __restrict__ pcstart,
-                                    const int4* __restrict__ kd, LevelGrid gp, LevelGrid g,
-                                    int32_t* __restrict__ mark) {
+                                    const int4* __restrict__ kd, LevelGrid gp, LevelGrid g, ConeMark mark) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncp * P) return;
     const int64_t pc = t / P;
@@ -282,7 +314,7 @@ __global__ void k_mark_parent_nodes(int64_t ncp, int P, int Ps, int Pt, int Pp, 
         const float ox = (float)((2 * (kk.x - 2 * kj.x) - 1) << sh);
         const float oy = (float)((2 * (kk.y - 2 * kj.y) - 1) << sh);
         const float oz = (float)((2 * (kk.z - 2 * kj.z) - 1) << sh);
-        mark[(int64_t)kb * g.C + classify_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz))] = 1;
+        mark.mark(kb, classify_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz)));
     }
 }
 
@@ -431,7 +463,7 @@ __global__ void k_mark_parent_nodes_tab(int64_t ncp, const int32_t* __restrict__
                                         const int32_t* __restrict__ cone_gidx, const int4* __restrict__ kp,
                                         const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
                                         const int32_t* __restrict__ tab_k, const int32_t* __restrict__ tab_list,
-                                        int C, int32_t* __restrict__ mark) {
+                                        ConeMark mark) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ncp * kTabList) return;
     const int64_t pc = t / kTabList;
@@ -442,7 +474,7 @@ __global__ void k_mark_parent_nodes_tab(int64_t ncp, const int32_t* __restrict__
     for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
         const int4 kk = kd[kb];
         const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
-        if (k < tab_k[row + o]) mark[(int64_t)kb * C + tab_list[(row + o) * kTabList + k]] = 1;
+        if (k < tab_k[row + o]) mark.mark(kb, tab_list[(row + o) * kTabList + k]);
     }
 }
 
@@ -460,6 +492,38 @@ __global__ void k_chunk_fill(const int32_t* __restrict__ start, int n, const int
         chunk_box[c] = b;
         chunk_start[c] = i;
     }
+}
+
+// Sparse levels: the hash set's keys become the cone list sorted by (box, gamma).
+__global__ void k_hash_flags(int64_t H, const unsigned long long* __restrict__ hkeys, int32_t* __restrict__ flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < H) flags[i] = hkeys[i] != kEmptyKey;
+}
+__global__ void k_hash_gather(int64_t H, const unsigned long long* __restrict__ hkeys,
+                              const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
+                              uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= H || !flags[i]) return;
+    keys[pos[i]] = hkeys[i];
+    vals[pos[i]] = pos[i];
+}
+__global__ void k_split_keys(int64_t nc, const uint64_t* __restrict__ keys, int64_t C, int32_t* __restrict__ cone_box,
+                             int32_t* __restrict__ cone_gam) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    cone_box[i] = (int32_t)(keys[i] / (uint64_t)C);
+    cone_gam[i] = (int32_t)(keys[i] % (uint64_t)C);
+}
+__global__ void k_box_cone_starts(int n, int64_t nc, const int32_t* __restrict__ cone_box, int32_t* __restrict__ bcs) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > n) return;
+    int64_t lo = 0, hi = nc;  // first cone of a box >= b
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cone_box[mid] < b) lo = mid + 1;
+        else hi = mid;
+    }
+    bcs[b] = (int32_t)lo;
 }
 
 __global__ void k_finalize_cones(int32_t* __restrict__ slot, const int32_t* __restrict__ pos, int64_t total, int C,
@@ -597,7 +661,7 @@ void build_node_tables(Plan& p, int dp) {
     Level& Lp = p.L[dp];
     Level& L = p.L[dp + 1];
     Lp.n_gam = 0;
-    if (Lp.nc == 0) return;
+    if (Lp.nc == 0 || Lp.g.C > (1 << 27)) return;  // tables pay off only for few distinct gamma
     const int C = Lp.g.C;
     int32_t* flags = dalloc<int32_t>(p, C);
     int32_t* pos = dalloc<int32_t>(p, C);
@@ -776,30 +840,82 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
     for (int d = 3; d <= D; ++d) {
         Level& L = p.L[d];
         const int64_t total = (int64_t)L.n * L.g.C;
-        if (total >= ((int64_t)1 << 31)) fail(IFGF_ERR_UNSUPPORTED, "dense cone table exceeds 2^31 entries");
-        L.slot = dalloc<int32_t>(p, total);
-        IFGF_CUDA(cudaMemsetAsync(L.slot, 0, sizeof(int32_t) * total, s));
-        IFGF_LAUNCH(k_mark_cousin_points, grid_for(N, kThreads), kThreads, 0, s, N, D, d, L.pbox, p.L[D].pbox,
-                    p.L[D].k, L.k, L.ncs, L.cs, p.off, L.g, L.slot);
-        if (d > 3) {
-            Level& Lp = p.L[d - 1];
-            if (Lp.nc > 0 && Lp.n_gam > 0)
-                IFGF_LAUNCH(k_mark_parent_nodes_tab, grid_for(Lp.nc * kTabList, kThreads), kThreads, 0, s, Lp.nc,
-                            Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, Lp.tab_k, Lp.tab_list, L.g.C, L.slot);
-            else if (Lp.nc > 0)
-                IFGF_LAUNCH(k_mark_parent_nodes, grid_for(Lp.nc * p.P, kThreads), kThreads, 0, s, Lp.nc, p.P, p.Ps,
-                            p.Pt, p.Pp, D, d, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, Lp.g, L.g, L.slot);
+        const bool dense = opt.cone_table == 1 || (opt.cone_table == 0 && total < ((int64_t)1 << 31));
+        if (dense && total >= ((int64_t)1 << 31)) fail(IFGF_ERR_UNSUPPORTED, "dense cone table exceeds 2^31 entries");
+        // one activation pass (both sources of Eq. (4)) into the given recorder
+        auto activate = [&](const ConeMark& cm) {
+            IFGF_LAUNCH(k_mark_cousin_points, grid_for(N, kThreads), kThreads, 0, s, N, D, d, L.pbox, p.L[D].pbox,
+                        p.L[D].k, L.k, L.ncs, L.cs, p.off, L.g, cm);
+            if (d > 3) {
+                Level& Lp = p.L[d - 1];
+                if (Lp.nc > 0 && Lp.n_gam > 0)
+                    IFGF_LAUNCH(k_mark_parent_nodes_tab, grid_for(Lp.nc * kTabList, kThreads), kThreads, 0, s, Lp.nc,
+                                Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, Lp.tab_k, Lp.tab_list, cm);
+                else if (Lp.nc > 0)
+                    IFGF_LAUNCH(k_mark_parent_nodes, grid_for(Lp.nc * p.P, kThreads), kThreads, 0, s, Lp.nc, p.P, p.Ps,
+                                p.Pt, p.Pp, D, d, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, Lp.g, L.g, cm);
+            }
+        };
+        if (dense) {
+            L.slot = dalloc<int32_t>(p, total);
+            IFGF_CUDA(cudaMemsetAsync(L.slot, 0, sizeof(int32_t) * total, s));
+            activate(ConeMark{L.slot, nullptr, 0, L.g.C, nullptr});
+            int32_t* cpos = dalloc<int32_t>(p, total);
+            exclusive_scan_i32(p, L.slot, cpos, total);
+            const int32_t last_pos = read_one(p, cpos + (total - 1));
+            const int32_t last_flag = read_one(p, L.slot + (total - 1));
+            L.nc = (int64_t)last_pos + last_flag;
+            L.cone_box = dalloc<int32_t>(p, L.nc);
+            L.cone_gam = dalloc<int32_t>(p, L.nc);
+            IFGF_LAUNCH(k_finalize_cones, grid_for(total, kThreads), kThreads, 0, s, L.slot, cpos, total, L.g.C,
+                        L.cone_box, L.cone_gam);
+            dfree_ptr(p, cpos);
+            L.bcs = dalloc<int32_t>(p, (size_t)L.n + 1);
+            IFGF_LAUNCH(k_box_cone_starts, grid_for((int64_t)L.n + 1, kThreads), kThreads, 0, s, L.n, L.nc, L.cone_box,
+                        L.bcs);
+        } else {
+            // hash set of (box, gamma) keys, grown until every insertion finds room
+            const int64_t guess = std::max<int64_t>({(int64_t)1 << 20, N / 2, d > 3 ? p.L[d - 1].nc : 0});
+            int64_t H = (int64_t)1 << 20;
+            while (H < 4 * guess && H < ((int64_t)1 << 31)) H <<= 1;
+            unsigned long long* hk = nullptr;
+            int* ovf = dalloc<int>(p, 1);
+            for (;;) {
+                hk = dalloc<unsigned long long>(p, (size_t)H);
+                IFGF_CUDA(cudaMemsetAsync(hk, 0xff, sizeof(unsigned long long) * H, s));
+                IFGF_CUDA(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+                activate(ConeMark{nullptr, hk, (unsigned long long)(H - 1), L.g.C, ovf});
+                if (!read_one(p, ovf)) break;
+                dfree_ptr(p, hk);
+                if (H >= ((int64_t)1 << 31)) fail(IFGF_ERR_OOM, "cone hash set cannot grow further");
+                H <<= 1;
+            }
+            dfree_ptr(p, ovf);
+            int32_t* flags = dalloc<int32_t>(p, (size_t)H);
+            int32_t* pos = dalloc<int32_t>(p, (size_t)H);
+            IFGF_LAUNCH(k_hash_flags, grid_for(H, kThreads), kThreads, 0, s, H, hk, flags);
+            exclusive_scan_i32(p, flags, pos, H);
+            L.nc = (int64_t)read_one(p, pos + (H - 1)) + read_one(p, flags + (H - 1));
+            uint64_t* keys = dalloc<uint64_t>(p, (size_t)std::max<int64_t>(L.nc, 1));
+            int32_t* vals = dalloc<int32_t>(p, (size_t)std::max<int64_t>(L.nc, 1));
+            IFGF_LAUNCH(k_hash_gather, grid_for(H, kThreads), kThreads, 0, s, H, hk, flags, pos, keys, vals);
+            dfree_ptr(p, hk);
+            dfree_ptr(p, flags);
+            dfree_ptr(p, pos);
+            const uint64_t maxkey = (uint64_t)L.n * (uint64_t)L.g.C;
+            int end_bit = 1;
+            while (end_bit < 64 && (maxkey >> end_bit) != 0) ++end_bit;
+            radix_sort_pairs(p, keys, vals, L.nc, end_bit);
+            L.cone_box = dalloc<int32_t>(p, std::max<int64_t>(L.nc, 1));
+            L.cone_gam = dalloc<int32_t>(p, std::max<int64_t>(L.nc, 1));
+            IFGF_LAUNCH(k_split_keys, grid_for(L.nc, kThreads), kThreads, 0, s, L.nc, keys, (int64_t)L.g.C, L.cone_box,
+                        L.cone_gam);
+            dfree_ptr(p, keys);
+            dfree_ptr(p, vals);
+            L.bcs = dalloc<int32_t>(p, (size_t)L.n + 1);
+            IFGF_LAUNCH(k_box_cone_starts, grid_for((int64_t)L.n + 1, kThreads), kThreads, 0, s, L.n, L.nc, L.cone_box,
+                        L.bcs);
         }
-        int32_t* cpos = dalloc<int32_t>(p, total);
-        exclusive_scan_i32(p, L.slot, cpos, total);
-        const int32_t last_pos = read_one(p, cpos + (total - 1));
-        const int32_t last_flag = read_one(p, L.slot + (total - 1));
-        L.nc = (int64_t)last_pos + last_flag;
-        L.cone_box = dalloc<int32_t>(p, L.nc);
-        L.cone_gam = dalloc<int32_t>(p, L.nc);
-        IFGF_LAUNCH(k_finalize_cones, grid_for(total, kThreads), kThreads, 0, s, L.slot, cpos, total, L.g.C,
-                    L.cone_box, L.cone_gam);
-        dfree_ptr(p, cpos);
         if (d < D && p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5) build_node_tables(p, d);
         if (p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5 && p.max_nrhs >= 4) {
             int32_t* cnt = dalloc<int32_t>(p, L.n);
@@ -815,6 +931,62 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
             dfree_ptr(p, cpos2);
         }
     }
+}
+
+namespace {
+// Child cones read by the parent-cone slice [lo, hi): [c_lo, c_hi).
+__global__ void k_slice_children(int ns, const int64_t* __restrict__ b, const int32_t* __restrict__ pcone_box,
+                                 const int32_t* __restrict__ pcstart, const int32_t* __restrict__ bcs,
+                                 int64_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const int64_t lo = b[i], hi = b[i + 1];
+    out[2 * i] = bcs[pcstart[pcone_box[lo]]];
+    out[2 * i + 1] = bcs[pcstart[pcone_box[hi - 1] + 1]];
+}
+}  // namespace
+
+// Arena cones needed when every propagation runs in k slices of equal parent-cone counts (the
+// slice boundaries are stored in the parent levels). With the child level at the start of the
+// arena, the parents go to its end, slices in descending order: slice [lo, hi) writes from
+// M - n_p + lo on while the children it and the later slices read lie below c_hi, so
+// M >= n_p - lo + c_hi. With the children at the end, ascending slices: M >= n_c + hi - c_lo.
+static int64_t arena_for_slices(Plan& p, int k) {
+    int64_t M = 0;
+    for (int d = 3; d <= p.D; ++d) M = std::max<int64_t>(M, p.L[d].nc);
+    for (int d = p.D; d >= 4; --d) {
+        Level& Lc = p.L[d];
+        Level& Lp = p.L[d - 1];
+        std::vector<int64_t> b;
+        const int ks = (int)std::max<int64_t>(1, std::min<int64_t>(k, Lp.nc));
+        for (int i = 0; i <= ks; ++i) b.push_back(Lp.nc * i / ks);
+        Lp.pslice = b;
+        if (Lp.nc == 0) continue;
+        int64_t* db = dalloc<int64_t>(p, b.size());
+        int64_t* dout = dalloc<int64_t>(p, 2 * (size_t)ks);
+        IFGF_CUDA(cudaMemcpyAsync(db, b.data(), sizeof(int64_t) * b.size(), cudaMemcpyHostToDevice, p.stream));
+        IFGF_LAUNCH(k_slice_children, grid_for(ks, 128), 128, 0, p.stream, ks, db, Lp.cone_box, Lp.cstart, Lc.bcs,
+                    dout);
+        std::vector<int64_t> c(2 * (size_t)ks);
+        IFGF_CUDA(cudaMemcpyAsync(c.data(), dout, sizeof(int64_t) * c.size(), cudaMemcpyDeviceToHost, p.stream));
+        IFGF_CUDA(cudaStreamSynchronize(p.stream));
+        dfree_ptr(p, db);
+        dfree_ptr(p, dout);
+        const bool child_at_start = (p.D - d) % 2 == 0;
+        for (int i = 0; i < ks; ++i) {
+            const int64_t need = child_at_start ? Lp.nc - b[i] + c[2 * i + 1] : Lc.nc + b[i + 1] - c[2 * i];
+            M = std::max(M, need);
+        }
+    }
+    return std::max<int64_t>(M, 1);
+}
+
+int64_t layout_arena(Plan& p, size_t budget_per_rhs) {
+    const size_t cone = (size_t)p.cstride * (p.precision == IFGF_PREC_MIXED ? 8 : 16);
+    int64_t M = arena_for_slices(p, 1);  // one launch per level: two full levels
+    if ((size_t)M * cone <= budget_per_rhs) return M;
+    M = arena_for_slices(p, 64);
+    return (size_t)M * cone <= budget_per_rhs ? M : 0;
 }
 
 }  // namespace ifgf

@@ -267,3 +267,57 @@ def test_density_blocks_equal_one_sweep():
     blocked = _apply(_plan(pts, kappa, precision="mixed", max_nrhs=10, rhs_block=4), A, "mixed")
     for r in range(10):
         assert oracle.rel_l2(blocked[r], full[r]) < 2e-5
+
+
+@pytest.mark.parametrize("prec,nrhs", [("mixed", 1), ("fp64", 1), ("mixed", 8)])
+def test_sorted_cone_lists_equal_dense_tables(prec, nrhs):
+    """The sorted per-box cone lists (used where a dense n_d x C_d table would be too large) give
+    the same cones as the dense table and, since every lookup returns the same cone, bit-identical
+    results; the cones also equal the oracle's."""
+    pts = W.spheroid(12_000, 0.5, 0.25, seed=41)
+    kappa = 2 * math.pi * 6
+    A = W.densities(pts.shape[1], nrhs, 42)
+    dense = _plan(pts, kappa, precision=prec, cone_table="dense", max_nrhs=nrhs)
+    srt = _plan(pts, kappa, precision=prec, cone_table="sorted", max_nrhs=nrhs)
+    for d in range(3, dense.D + 1):
+        np.testing.assert_array_equal(dense.query(ifgf.Q.CONE_BOX, d), srt.query(ifgf.Q.CONE_BOX, d))
+        np.testing.assert_array_equal(dense.query(ifgf.Q.CONE_GAMMA, d), srt.query(ifgf.Q.CONE_GAMMA, d))
+    a = _apply(dense, A, prec)
+    b = _apply(srt, A, prec)
+    assert dense.status() == 0 and srt.status() == 0
+    np.testing.assert_array_equal(a, b)
+    if prec == "mixed" and nrhs == 1:
+        assert_same_tree(srt, oracle.Plan(pts, kappa))
+
+
+@pytest.mark.parametrize("name", ["sphere512", "sphere512_laplace"])
+def test_full_size_sphere512_sampled(name):
+    """The 512-wavelength, 25,165,824-point sphere (sorted cone lists at the coarse levels) and its
+    Laplace repeat: error on 500 seeded targets against the direct sum."""
+    w = W.make(name)
+    pts, kappa = w.points(), w.kappa
+    dens = w.densities()
+    tgt = W.targets(w.n, 500, w.seed + 200)
+    gp = _plan(pts, kappa, precision="mixed")
+    got = _apply(gp, dens, "mixed")[:, tgt]
+    assert gp.status() == 0
+    exact = oracle.direct_sum(pts, kappa, dens, tgt)
+    err = oracle.rel_l2(got, exact)
+    print(f"{name}: D = {gp.D}, rel. L2 error on {len(tgt)} targets = {err:.3e}")
+    assert err < 5e-4
+
+
+def test_full_size_oblate128_many_densities():
+    """The 128-wavelength (a, a, a/4) spheroid, N = 6,291,456, 32 densities on the tensor-core path:
+    error of every density on 100 seeded targets against the direct sum."""
+    w = W.make("oblate128")
+    pts, kappa = w.points(), w.kappa
+    dens = w.densities()
+    tgt = W.targets(w.n, 100, w.seed + 200)
+    gp = _plan(pts, kappa, precision="mixed", max_nrhs=w.nrhs)
+    got = _apply(gp, dens, "mixed")[:, tgt]
+    assert gp.status() == 0
+    exact = oracle.direct_sum(pts, kappa, dens, tgt)
+    worst = max(oracle.rel_l2(got[r], exact[r]) for r in range(w.nrhs))
+    print(f"oblate128 x 32: worst density rel. L2 error on {len(tgt)} targets = {worst:.3e}")
+    assert worst < 5e-4
