@@ -401,90 +401,108 @@ k_prop_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __
     }
 }
 
-// Propagation from the node tables of the parent level: the geometry of every (cone index,
-// child octant, node) was computed once at plan time, so an evaluation is a table read, the
-// child cone's slot, the interpolant contraction and the complex ratio. A thread evaluates one
-// segment: up to kSegLen nodes of one (parent cone, child) pair that fall in the same child
-// cone, sharing the coefficient loads of that cone.
-constexpr int kSegCones = 8;     // parent cones per block
-constexpr int kSegThreads = 128;
+// Propagation from the node tables of the parent level (orders (3,5,5), mixed precision): the
+// geometry of every (cone index, child octant, node) was computed once at plan time, so an
+// evaluation is a table read, the child cone's slot, the interpolant contraction and the complex
+// ratio. One warp per parent cone, no block-wide barrier: the warp resolves its children's rows
+// and child-cone slots, stages the child cones' coefficient blocks in shared memory with
+// coalesced asynchronous copies, evaluates half-segments (up to 4 nodes of one child cone per
+// lane, sharing each coefficient row), sums the children in order and forms the coefficients,
+// synchronising only itself.
+constexpr int kWarpCones = 2;  // warps (parent cones) per block
+constexpr int kWarpStage = 8; // child-cone coefficient blocks staged in shared memory per warp
+constexpr int kStage4 = 39;    // float4 per staged block (38 used; odd, so lanes reading different
+                               // blocks at one offset hit different banks)
 template <int PS, int PT, int PP>
-__global__ void __launch_bounds__(kSegThreads, 3)
-k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
-               const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
-               ConeMap cm, const float4* __restrict__ tab_t,
-               const float2* __restrict__ tab_r, const int32_t* __restrict__ tab_k,
-               const int32_t* __restrict__ tab_list, const int16_t* __restrict__ tab_perm,
-               const int32_t* __restrict__ tab_nseg, const int32_t* __restrict__ tab_seg,
-               const float2* __restrict__ cchild, float2* __restrict__ cparent, const float* __restrict__ W,
-               int cstride, int nrhs, int* __restrict__ status) {
+__global__ void __launch_bounds__(32 * kWarpCones, 9)
+k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
+                const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
+                ConeMap cm, const float4* __restrict__ tab_t, const float2* __restrict__ tab_r,
+                const int32_t* __restrict__ tab_k, const int32_t* __restrict__ tab_list,
+                const int16_t* __restrict__ tab_perm, const int32_t* __restrict__ tab_nseg,
+                const int32_t* __restrict__ tab_seg, const float2* __restrict__ cchild, float2* __restrict__ cparent,
+                const float* __restrict__ W, int cstride, int nrhs, int* __restrict__ status) {
     constexpr int P = PS * PT * PP;
-    constexpr int NC = kSegCones;
-    constexpr int R = kSegLen;
-    // vals[c][ch][n]: child ch's contribution at node n of cone c; after the sum over children,
-    // vals[c][0] holds the node values and vals[c][1] the first transform stage
-    __shared__ float2 vals[NC][8][P];
-    __shared__ int s_goff[NC * 8 + 1], s_kb0[NC], s_nch[NC], s_row[NC][8];
-    __shared__ int s_slot[NC][8][kTabList];
-    const int tid = threadIdx.x;
+    constexpr int R = kSegLen / 2;  // a thread evaluates half a segment
+    __shared__ float2 s_vals[kWarpCones][8][P];
+    __shared__ float4 s_cbuf[kWarpCones][kWarpStage * kStage4];
+    __shared__ int s_slot_w[kWarpCones][8][kTabList];  // global slot, -1 missing, -2 - j staged as block j
+    __shared__ int s_row_w[kWarpCones][8], s_goff_w[kWarpCones][9], s_koff_w[kWarpCones][9];
+    __shared__ int s_dsl_w[kWarpCones][kWarpStage];  // global slot of every staged block
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t pc = (int64_t)blockIdx.x * kWarpCones + warp;
+    if (pc >= ncp) return;  // the whole warp leaves; nothing below synchronises the block
     const int r = blockIdx.y;
-    const int64_t pc0 = (int64_t)blockIdx.x * NC;
-    if (tid < NC) {
-        const int c = tid;
-        const int64_t pc = pc0 + c;
-        int nch = 0;
-        if (pc < ncp) {
-            const int jb = pcone_box[pc];
-            const int k0 = pcstart[jb];
-            nch = pcstart[jb + 1] - k0;
-            s_kb0[c] = k0;
-            const int g8 = cone_gidx[pc] * 8;
-            const int4 kj = kp[jb];
-            for (int ch = 0; ch < nch; ++ch) {
-                const int4 kk = kd[k0 + ch];
-                s_row[c][ch] = g8 + ((kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2));
-            }
-        }
-        s_nch[c] = nch;
+    float2 (*vals)[P] = s_vals[warp];
+    int (*s_slot)[kTabList] = s_slot_w[warp];
+    int* s_row = s_row_w[warp];
+    int* s_goff = s_goff_w[warp];
+    const int jb = pcone_box[pc];
+    const int k0 = pcstart[jb], nch = pcstart[jb + 1] - k0;
+    const int g8 = cone_gidx[pc] * 8;
+    int* s_koff = s_koff_w[warp];
+    float4* cbuf = s_cbuf[warp];
+    int nseg = 0, K = 0;
+    if (lane < nch) {
+        const int4 kj = kp[jb];
+        const int4 kk = kd[k0 + lane];
+        const int row = g8 + ((kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2));
+        s_row[lane] = row;
+        nseg = __ldg(&tab_nseg[row]);
+        K = __ldg(&tab_k[row]);
     }
-    __syncthreads();
-    if (tid < NC * 8) {
-        const int c = tid / 8, ch = tid % 8;
-        s_goff[tid + 1] = ch < s_nch[c] ? __ldg(&tab_nseg[s_row[c][ch]]) : 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        s_goff[0] = 0;
-        for (int g = 0; g < NC * 8; ++g) s_goff[g + 1] += s_goff[g];
-    }
-    // child-cone slots of every (cone, child) group, once per block; their coefficient blocks
-    // are prefetched into L2 while the slots resolve
-    for (int x = tid; x < NC * 8 * kTabList; x += kSegThreads) {
-        const int k = x % kTabList, g = x / kTabList;
-        const int c = g / 8, ch = g % 8;
-        if (ch >= s_nch[c]) continue;
-        const int row = s_row[c][ch];
-        if (k >= __ldg(&tab_k[row])) continue;
-        const int sl = cm.find(s_kb0[c] + ch, __ldg(&tab_list[(int64_t)row * kTabList + k]));
-        s_slot[c][ch][k] = sl;
-        if (sl >= 0) {
-            const char* blk = reinterpret_cast<const char*>(cchild + ((int64_t)sl * nrhs + r) * cstride);
+    int incl = nseg, kincl = K;  // inclusive prefixes over the children (lanes 0..7)
 #pragma unroll
-            for (int off = 0; off < P * 8; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(blk + off));
+    for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o), w = __shfl_up_sync(0xffffffffu, kincl, o);
+        if (lane >= o) {
+            incl += v;
+            kincl += w;
         }
     }
-    __syncthreads();
-    const int total = s_goff[NC * 8];
-    for (int item = tid; item < total; item += kSegThreads) {
-        int g = 0;  // last group with s_goff[g] <= item
-#pragma unroll
-        for (int step = 32; step >= 1; step >>= 1)
-            if (g + step < NC * 8 && s_goff[g + step] <= item) g += step;
-        const int c = g / 8, ch = g % 8;
-        const int64_t rowP = (int64_t)s_row[c][ch] * P;
-        const int sg = __ldg(&tab_seg[rowP + (item - s_goff[g])]);
-        const int j0 = sg & 0xff, len = (sg >> 8) & 0xff, kl = sg >> 16;
-        const int s = (unsigned)kl < (unsigned)kTabList ? s_slot[c][ch][kl] : -1;
+    if (lane < 8) {
+        s_goff[lane + 1] = incl;
+        s_koff[lane + 1] = kincl;
+    }
+    if (lane == 0) s_goff[0] = s_koff[0] = 0;
+    __syncwarp();
+    // child-cone slots, one list entry per lane; the first kWarpStage distinct blocks (the
+    // children's lists are disjoint) are copied to shared memory with coalesced asynchronous
+    // copies, the rest are read from global memory
+    for (int ch = 0; ch < nch; ++ch) {
+        const int row = s_row[ch];
+        const int Kc = s_koff[ch + 1] - s_koff[ch];
+        const int a = __ldg(&tab_list[(int64_t)row * kTabList + lane]);
+        if (lane < Kc) {
+            const int sl = cm.find(k0 + ch, a);
+            const int j = s_koff[ch] + lane;
+            const bool staged = sl >= 0 && j < kWarpStage;
+            s_slot[ch][lane] = staged ? -2 - j : sl;
+            if (j < kWarpStage) s_dsl_w[warp][j] = sl;
+        }
+    }
+    __syncwarp();
+    const int nst = min(s_koff[nch], kWarpStage);
+    for (int x = lane; x < nst * 38; x += 32) {
+        const int j = x / 38, q = x - (x / 38) * 38;
+        const int sl = s_dsl_w[warp][j];
+        if (sl < 0) continue;  // missing cone: reported where it is used
+        const float4* src = reinterpret_cast<const float4*>(cchild + ((int64_t)sl * nrhs + r) * cstride) + q;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(cbuf + j * kStage4 + q);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    const int total = 2 * s_goff[nch];
+    for (int item = lane; item < total; item += 32) {
+        const int seg = item >> 1, half = item & 1;
+        int ch = 0;
+        while (ch + 1 < nch && s_goff[ch + 1] <= seg) ++ch;
+        const int64_t rowP = (int64_t)s_row[ch] * P;
+        const int sg = __ldg(&tab_seg[rowP + (seg - s_goff[ch])]);
+        const int j0 = (sg & 0xff) + R * half, len = min(R, ((sg >> 8) & 0xff) - R * half), kl = sg >> 16;
+        if (len <= 0) continue;
+        const int sv = (unsigned)kl < (unsigned)kTabList ? s_slot[ch][kl] : -1;
         float ts[R], tt[R], tp[R];
         float2 ratio[R], F[R];
 #pragma unroll
@@ -496,70 +514,66 @@ k_prop_tab_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
             tp[q] = t4.z;
             ratio[q] = __ldg(&tab_r[e]);
         }
-        if (s < 0) {
+        if (sv <= -2) {
+            interp_f32_seg<PS, PT, PP, R, true>(reinterpret_cast<const float2*>(cbuf + (-2 - sv) * kStage4), ts, tt,
+                                                tp, F);
+        } else if (sv >= 0) {
+            interp_f32_seg<PS, PT, PP, R>(cchild + ((int64_t)sv * nrhs + r) * cstride, ts, tt, tp, F);
+        } else {
             set_status(status, IFGF_ERR_INTERNAL);
 #pragma unroll
             for (int q = 0; q < R; ++q) F[q] = make_float2(0.f, 0.f);
-        } else {
-            interp_f32_seg<PS, PT, PP, R>(cchild + ((int64_t)s * nrhs + r) * cstride, ts, tt, tp, F);
         }
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (q < len) vals[c][ch][__ldg(&tab_perm[rowP + j0 + q])] = cmul(F[q], ratio[q]);
+            if (q < len) vals[ch][__ldg(&tab_perm[rowP + j0 + q])] = cmul(F[q], ratio[q]);
     }
-    __syncthreads();
+    __syncwarp();
     const float* Ws = W;
     const float* Wt = W + PS * PS;
     const float* Wp = Wt + PT * PT;
-    for (int x = tid; x < NC * P; x += kSegThreads) {
-        const int c = x / P, n = x - (x / P) * P;
-        const int nch = s_nch[c];
-        float2 a = make_float2(0.f, 0.f);
-        for (int ch = 0; ch < nch; ++ch) {
-            a.x += vals[c][ch][n].x;
-            a.y += vals[c][ch][n].y;
+    for (int n = lane; n < P; n += 32) {  // sum over children, in child order
+        float2 a = vals[0][n];
+        for (int ch = 1; ch < nch; ++ch) {
+            a.x += vals[ch][n].x;
+            a.y += vals[ch][n].y;
         }
-        vals[c][0][n] = a;
+        vals[0][n] = a;
     }
-    __syncthreads();
-    for (int x = tid; x < NC * P; x += kSegThreads) {
-        const int c = x / P, n = x - (x / P) * P;
+    __syncwarp();
+    for (int n = lane; n < P; n += 32) {
         const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
         float2 acc = make_float2(0.f, 0.f);
-        const float2* rw = &vals[c][0][(qa * PT + qb) * PP];
+        const float2* rw = &vals[0][(qa * PT + qb) * PP];
 #pragma unroll
         for (int k = 0; k < PP; ++k) {
             const float w = Wp[qc * PP + k];
             acc.x = fmaf(w, rw[k].x, acc.x);
             acc.y = fmaf(w, rw[k].y, acc.y);
         }
-        vals[c][1][n] = acc;
+        vals[1][n] = acc;
     }
-    __syncthreads();
-    for (int x = tid; x < NC * P; x += kSegThreads) {
-        const int c = x / P, n = x - (x / P) * P;
+    __syncwarp();
+    for (int n = lane; n < P; n += 32) {
         const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < PT; ++j) {
             const float w = Wt[qb * PT + j];
-            const float2 v = vals[c][1][(qa * PT + j) * PP + qc];
+            const float2 v = vals[1][(qa * PT + j) * PP + qc];
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
         }
-        vals[c][0][n] = acc;
+        vals[2][n] = acc;
     }
-    __syncthreads();
-    for (int x = tid; x < NC * P; x += kSegThreads) {
-        const int c = x / P, n = x - (x / P) * P;
-        const int64_t pc = pc0 + c;
-        if (pc >= ncp) continue;
+    __syncwarp();
+    for (int n = lane; n < P; n += 32) {
         const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
             const float w = Ws[qa * PS + i];
-            const float2 v = vals[c][0][(i * PT + qb) * PP + qc];
+            const float2 v = vals[2][(i * PT + qb) * PP + qc];
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
         }
@@ -1448,8 +1462,8 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                 constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
                               TP = PS * PT * PP <= 75 ? PP : 5;
                 for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                    IFGF_LAUNCH((k_prop_tab_f32<TS, TT, TP>), dim3((unsigned)((n + kSegCones - 1) / kSegCones), nrhs),
-                                kSegThreads, 0, s, n, Lp.cone_box + lo, Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k,
+                    IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP>), dim3((unsigned)((n + kWarpCones - 1) / kWarpCones), nrhs),
+                                32 * kWarpCones, 0, s, n, Lp.cone_box + lo, Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k,
                                 L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, Lp.tab_nseg,
                                 Lp.tab_seg, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
                 });

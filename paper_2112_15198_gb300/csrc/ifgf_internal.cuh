@@ -470,7 +470,9 @@ __device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float
 // The contraction of interp_f32 for R points of one cone: every coefficient row is loaded
 // once and applied to all R points, so the coefficient bytes moved into registers per point
 // drop by R. Row (a, b) enters point q with weight T_a(ts_q) T_b(tt_q).
-template <int PS, int PT, int PP, int R>
+// kShared: the coefficient block was staged in shared memory (same layout) and is read with
+// plain loads; otherwise it is read from global memory through the read-only path.
+template <int PS, int PT, int PP, int R, bool kShared = false>
 __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, const float* ts, const float* tt,
                                                const float* tp, float2* out) {
     float Ts[R][PS], Tt[R][PT], Tp[R][PP];
@@ -495,10 +497,14 @@ __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, con
     constexpr int NR = PS * PT;
     if constexpr (PP == 5) {
         const float4* c4 = reinterpret_cast<const float4*>(c);
+        auto ld4 = [&](int i) -> float4 {
+            if constexpr (kShared) return c4[i];
+            else return __ldg(c4 + i);
+        };
 #pragma unroll
         for (int m = 0; m < NR / 2; ++m) {
-            const float4 v0 = __ldg(c4 + 5 * m + 0), v1 = __ldg(c4 + 5 * m + 1), v2 = __ldg(c4 + 5 * m + 2);
-            const float4 v3 = __ldg(c4 + 5 * m + 3), v4 = __ldg(c4 + 5 * m + 4);
+            const float4 v0 = ld4(5 * m + 0), v1 = ld4(5 * m + 1), v2 = ld4(5 * m + 2);
+            const float4 v3 = ld4(5 * m + 3), v4 = ld4(5 * m + 4);
             const float2 r0[5] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
                                   make_float2(v1.z, v1.w), make_float2(v2.x, v2.y)};
             const float2 r1[5] = {make_float2(v2.z, v2.w), make_float2(v3.x, v3.y), make_float2(v3.z, v3.w),
@@ -507,8 +513,10 @@ __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, con
             fold(2 * m + 1, r1);
         }
         if constexpr (NR % 2 == 1) {
-            const float4 v0 = __ldg(c4 + 5 * (NR / 2) + 0), v1 = __ldg(c4 + 5 * (NR / 2) + 1);
-            const float2 v2 = __ldg(c + 10 * (NR / 2) + 4);
+            const float4 v0 = ld4(5 * (NR / 2) + 0), v1 = ld4(5 * (NR / 2) + 1);
+            float2 v2;
+            if constexpr (kShared) v2 = c[10 * (NR / 2) + 4];
+            else v2 = __ldg(c + 10 * (NR / 2) + 4);
             const float2 r0[5] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
                                   make_float2(v1.z, v1.w), v2};
             fold(NR - 1, r0);
@@ -518,7 +526,10 @@ __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, con
         for (int rr = 0; rr < NR; ++rr) {
             float2 row[PP];
 #pragma unroll
-            for (int k = 0; k < PP; ++k) row[k] = __ldg(c + rr * PP + k);
+            for (int k = 0; k < PP; ++k) {
+                if constexpr (kShared) row[k] = c[rr * PP + k];
+                else row[k] = __ldg(c + rr * PP + k);
+            }
             // rr is not a compile-time constant here: weights by explicit selection
             const int a = rr / PT, b = rr - (rr / PT) * PT;
 #pragma unroll
