@@ -150,6 +150,23 @@ def traffic_record(kernel: str):
     return None
 
 
+def max_over_ranks(x: float, pg, device) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's); x itself when
+    there is one rank."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ws: int, n: int, nrhs: int, ms_step: float) -> float:
+    """Points of all ranks per second: every rank solves its own full problem (replicas)."""
+    return ws * n * nrhs / (ms_step / 1e3)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -259,12 +276,8 @@ def main():
     kt = ifgf.timing_collect()
     ifgf.timing_enable(False)
     clk = clocks.stop()
-    ms_step = total_ms / args.steps
-    if pg:
-        t = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = ws * w.n * w.nrhs / (ms_step / 1e3)
+    ms_step = max_over_ranks(total_ms / args.steps, pg, dev)
+    value = whole_job_value(ws, w.n, w.nrhs, ms_step)
 
     # ---- apply-only throughput on a persistent plan (context) ------------------------
     plan = ifgf.Plan(P, w.kappa, precision=args.precision, max_nrhs=w.nrhs)
@@ -304,10 +317,7 @@ def main():
         if it >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_step = statistics.mean(e2e_ms)
-    if pg:
-        t = torch.tensor([e2e_step], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(e2e_step, pg, dev)
     h2d = P_host.numel() * P_host.element_size() + A_host.numel() * A_host.element_size()
     d2h = out_host.numel() * out_host.element_size()
 
@@ -347,7 +357,7 @@ def main():
            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
            "config": config_of(w, args.precision, D),
-           "e2e": {"value": ws * w.n * w.nrhs / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "e2e": {"value": whole_job_value(ws, w.n, w.nrhs, e2e_step), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
            "apply_only": {"value": w.n * w.nrhs / (statistics.median(ap_ms) / 1e3), "unit": UNIT,
