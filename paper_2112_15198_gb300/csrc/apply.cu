@@ -153,48 +153,121 @@ __device__ __forceinline__ T2 cheb_coeffs_smem(T2* f, T2* g, const R* __restrict
 //   F(y) = sum_{x' in B} a(x') g_k(y, x'),  g_k = G(y,x')/G(y,x_k)  (Eq. (3)),
 // with y = x_k + (h/s) yhat and u = (x' - x_k)/h:
 //   g_k = exp(i kappa h (s|u|^2 - 2 yhat.u) / (|yhat - s u| + 1)) / |yhat - s u|.
+
+// LevelDEvaluations with one block per leaf box: the box's sources (offset from the centre in
+// units of h, |u|^2 and the density) are staged in shared memory once and swept by every
+// (cone, node) of the box, up to 32 cones at a time. For the node x = x_k + (h/s) y (|y| = 1)
+// and the source x' = x_k + h u, |x - x'|^2 / r^2 = q = 1 + s (s |u|^2 - 2 y.u), so
+//     g_k(x, x') = q^(-1/2) exp(i kappa h (s |u|^2 - 2 y.u) / (1 + q^(1/2))),
+// free of cancellation; then the coefficient transform of each cone by one warp.
+constexpr int kLeafThreads = 256;
+constexpr int kLeafSrc = 256;    // sources staged per pass
+constexpr int kLeafCones = 32;   // cones of the box per pass
 template <int PS, int PT, int PP>
-__global__ void k_leaf_f32(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam, LevelGrid g,
-                           const int32_t* __restrict__ startD, const float4* __restrict__ off,
-                           const float2* __restrict__ as, int64_t N, float kh, float hinv,
-                           const float* __restrict__ W, float2* __restrict__ coef, int cstride, int nrhs) {
+__global__ void __launch_bounds__(kLeafThreads)
+k_leaf_box_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ cone_gam, LevelGrid g,
+               const int32_t* __restrict__ startD, const float4* __restrict__ off, const float2* __restrict__ as,
+               int64_t N, float kh, float hinv, const float* __restrict__ W, float2* __restrict__ coef, int cstride,
+               int nrhs) {
     constexpr int P = PS * PT * PP;
-    __shared__ float2 f[P], tmp[P];
-    const int cone = blockIdx.x;
+    constexpr int NW = kLeafThreads / 32;
+    __shared__ float4 s_u[kLeafSrc];   // (u, |u|^2)
+    __shared__ float2 s_a[kLeafSrc];
+    __shared__ float2 f[kLeafCones][P];
+    __shared__ float2 tmp[NW][P];
+    const int b = blockIdx.x;
     const int r = blockIdx.y;
-    const int n = threadIdx.x;
-    const int b = cone_box[cone];
-    if (n < P) {
-        const int gam = cone_gam[cone];
-        const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
-        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
-        const float s = g.snode[is * PS + ia];
-        const float st = g.stn[it * PT + ib], ct = g.ctn[it * PT + ib];
-        const float yx = st * g.cpn[ip * PP + ic], yy = st * g.spn[ip * PP + ic], yz = ct;
-        const float2* ar = as + (int64_t)r * N;
-        float2 acc = make_float2(0.f, 0.f);
-        const int j1 = startD[b + 1];
-        for (int j = startD[b]; j < j1; ++j) {
-            const float4 o = __ldg(&off[j]);
-            const float ux = o.x * hinv, uy = o.y * hinv, uz = o.z * hinv;
-            const float wx = fmaf(-s, ux, yx), wy = fmaf(-s, uy, yy), wz = fmaf(-s, uz, yz);
-            const float q = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-            const float rq = rsqrtf(q);
-            const float uu = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-            const float yu = fmaf(yx, ux, fmaf(yy, uy, yz * uz));
-            const float num = fmaf(s, uu, -2.f * yu);
-            const float ph = kh * __fdividef(num, fmaf(q, rq, 1.f));
-            const float2 e = cis_f32(ph);
-            const float2 gk = make_float2(e.x * rq, e.y * rq);
-            const float2 aj = __ldg(&ar[j]);
-            acc = __ffma2_rn(make_float2(aj.x, aj.x), gk, acc);
-            acc = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(gk.y, gk.x), acc);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c0 = bcs[b], c1 = bcs[b + 1];
+    if (c0 == c1) return;
+    const int j0 = startD[b], j1 = startD[b + 1];
+    const float2* ar = as + (int64_t)r * N;
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int cc = c0; cc < c1; cc += kLeafCones) {
+        const int ncc = min(kLeafCones, c1 - cc);
+        const int items = ncc * P;
+        for (int t0 = j0; t0 < j1; t0 += kLeafSrc) {
+            const int nt = min(kLeafSrc, j1 - t0);
+            __syncthreads();
+            if (tid < nt) {
+                const float4 o = __ldg(&off[t0 + tid]);
+                const float ux = o.x * hinv, uy = o.y * hinv, uz = o.z * hinv;
+                s_u[tid] = make_float4(ux, uy, uz, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
+                s_a[tid] = __ldg(&ar[t0 + tid]);
+            }
+            __syncthreads();
+            for (int item = tid; item < items; item += kLeafThreads) {
+                const int cl = item / P, n = item - (item / P) * P;
+                const int gam = __ldg(&cone_gam[cc + cl]);
+                const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
+                const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+                const float sn = __ldg(&g.snode[is * PS + ia]);
+                const float st = __ldg(&g.stn[it * PT + ib]), ct = __ldg(&g.ctn[it * PT + ib]);
+                const float yx = st * __ldg(&g.cpn[ip * PP + ic]), yy = st * __ldg(&g.spn[ip * PP + ic]), yz = ct;
+                float2 acc = t0 == j0 ? make_float2(0.f, 0.f) : f[cl][n];
+#pragma unroll 4
+                for (int j = 0; j < nt; ++j) {
+                    const float4 u = s_u[j];
+                    const float yu = fmaf(yx, u.x, fmaf(yy, u.y, yz * u.z));
+                    const float num = fmaf(sn, u.w, -2.f * yu);
+                    const float q = fmaf(sn, num, 1.f);
+                    const float rq = rsqrtf(q);
+                    const float2 e = cis_f32(kh * __fdividef(num, fmaf(q, rq, 1.f)));
+                    const float2 gk = make_float2(e.x * rq, e.y * rq);
+                    const float2 aj = s_a[j];
+                    acc = __ffma2_rn(make_float2(aj.x, aj.x), gk, acc);
+                    acc = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(gk.y, gk.x), acc);
+                }
+                f[cl][n] = acc;
+            }
         }
-        f[n] = acc;
+        __syncthreads();
+        for (int cl = warp; cl < ncc; cl += NW) {  // coefficient transform, one warp per cone
+            float2* fv = f[cl];
+            float2* tv = tmp[warp];
+            for (int n = lane; n < P; n += 32) {
+                const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < PP; ++k) {
+                    const float w = Wp[qc * PP + k];
+                    const float2 v = fv[(qa * PT + qb) * PP + k];
+                    a.x = fmaf(w, v.x, a.x);
+                    a.y = fmaf(w, v.y, a.y);
+                }
+                tv[n] = a;
+            }
+            __syncwarp();
+            for (int n = lane; n < P; n += 32) {
+                const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < PT; ++k) {
+                    const float w = Wt[qb * PT + k];
+                    const float2 v = tv[(qa * PT + k) * PP + qc];
+                    a.x = fmaf(w, v.x, a.x);
+                    a.y = fmaf(w, v.y, a.y);
+                }
+                fv[n] = a;
+            }
+            __syncwarp();
+            for (int n = lane; n < P; n += 32) {
+                const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < PS; ++k) {
+                    const float w = Ws[qa * PS + k];
+                    const float2 v = fv[(k * PT + qb) * PP + qc];
+                    a.x = fmaf(w, v.x, a.x);
+                    a.y = fmaf(w, v.y, a.y);
+                }
+                coef[((int64_t)(cc + cl) * nrhs + r) * cstride + n] = a;
+            }
+            __syncwarp();
+        }
     }
-    __syncthreads();
-    const float2 c = cheb_coeffs_smem<PS, PT, PP>(f, tmp, W, n);
-    if (n < P) coef[((int64_t)cone * nrhs + r) * cstride + n] = c;
 }
 
 template <int PS, int PT, int PP>
@@ -1438,9 +1511,9 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
         if (LD.nc > 0)
             {
                 TimedScope ts_(TK_LEAF, s);
-                IFGF_LAUNCH((k_leaf_f32<PS, PT, PP>), dim3((unsigned)LD.nc, nrhs), BT, 0, s, LD.cone_box, LD.cone_gam,
-                            LD.g, LD.start, p.off, as, N, kh, 1.0f / LD.g.hg, p.Wf, (float2*)level_coef(p, D, nrhs),
-                            p.cstride, nrhs);
+                IFGF_LAUNCH((k_leaf_box_f32<PS, PT, PP>), dim3((unsigned)LD.n, nrhs), kLeafThreads, 0, s, LD.bcs,
+                            LD.cone_gam, LD.g, LD.start, p.off, as, N, kh, 1.0f / LD.g.hg, p.Wf,
+                            (float2*)level_coef(p, D, nrhs), p.cstride, nrhs);
             }
         for (int d = D; d >= 3; --d) {
             Level& L = p.L[d];
