@@ -116,6 +116,13 @@ struct Level {
     int32_t* tab_nseg = nullptr;   // [n_gam*8]
     int32_t* tab_seg = nullptr;    // [n_gam*8*P]
     int32_t* tab_run = nullptr;    // [n_gam*8][kTabList+1] first segment of each child cone, then nseg
+    // Levels without node tables (mixed precision, orders (3,5,5)): relevant cones grouped by
+    // cone index. gorder lists them by (block of boxes, gamma, box); gchunk[c]..gchunk[c+1] is a
+    // chunk of at most kChunkBoxes cones of one gamma, whose node classification seen from the
+    // eight child octants is computed once for the whole chunk (activation of the next level).
+    int64_t n_gchunk = 0;
+    int32_t* gorder = nullptr;     // [nc]
+    int32_t* gchunk = nullptr;     // [n_gchunk+1]
     // Target chunks of <= 16 points of one box (tensor-core interpolation with many densities).
     int64_t nchunk = 0;
     int32_t* chunk_box = nullptr;
@@ -125,6 +132,7 @@ struct Level {
 };
 constexpr int kTabList = 32;
 constexpr int kSegLen = 8;  // nodes of one child cone evaluated by one thread
+constexpr int kChunkBoxes = 8;  // cones (of one gamma, different boxes) per chunk
 
 struct Plan {
     int64_t N = 0;

@@ -457,6 +457,86 @@ __global__ void k_node_lists(int P, float4* __restrict__ tab_t, float2* __restri
     }
 }
 
+// Cones grouped by cone index: key = (box >> bb_shift, gamma), stably sorted (the cone list is
+// already in box order), then cut into chunks of at most kChunkBoxes cones of one key.
+__global__ void k_gamma_keys(int64_t nc, const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam,
+                             int bb_shift, int C, uint64_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    keys[i] = (uint64_t)(cone_box[i] >> bb_shift) * (uint64_t)C + (uint64_t)cone_gam[i];
+    vals[i] = (int32_t)i;
+}
+__global__ void k_gamma_chunk_flags(int64_t n, const uint64_t* __restrict__ keys, int32_t* __restrict__ flags) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int f = 1;
+    if (i > 0 && keys[i] == keys[i - 1]) {
+        int64_t lo = 0, hi = i;  // first index with this key
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (keys[mid] < keys[i]) lo = mid + 1;
+            else hi = mid;
+        }
+        f = (i - lo) % kChunkBoxes == 0;
+    }
+    flags[i] = f;
+}
+__global__ void k_gamma_chunk_fill(int64_t n, const int32_t* __restrict__ flags, const int32_t* __restrict__ pos,
+                                   int32_t* __restrict__ gchunk) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (flags[i]) gchunk[pos[i]] = (int32_t)i;
+    if (i == n - 1) gchunk[pos[i] + flags[i]] = (int32_t)n;  // end of the last chunk
+}
+
+// Activation from the nodes of the relevant parent cones, one block per chunk: the child cone of
+// node n seen from child octant o is classified once for the chunk (it depends on (gamma, o, n)
+// only) and marked in every child at octant o of the chunk's boxes.
+__global__ void __launch_bounds__(32 * kChunkBoxes)
+k_mark_parent_nodes_chunk(const int32_t* __restrict__ gchunk, const int32_t* __restrict__ gorder,
+                          const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
+                          const int4* __restrict__ kp, const int32_t* __restrict__ pcstart,
+                          const int4* __restrict__ kd, int D, int d, LevelGrid gp, LevelGrid g, ConeMark mark) {
+    constexpr int Ps = 3, Pt = 5, Pp = 5, P = 75;
+    __shared__ int s_alpha[8][P];
+    __shared__ int s_omask;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c0 = gchunk[blockIdx.x], nb = gchunk[blockIdx.x + 1] - c0;
+    if (tid == 0) s_omask = 0;
+    __syncthreads();
+    const int gam = pcone_gam[gorder[c0]];
+    int jb = -1, k0 = 0, nch = 0;
+    int4 kj = make_int4(0, 0, 0, 0);
+    if (warp < nb) {
+        jb = pcone_box[gorder[c0 + warp]];
+        k0 = pcstart[jb];
+        nch = pcstart[jb + 1] - k0;
+        kj = kp[jb];
+        if (lane < nch) {
+            const int4 kk = kd[k0 + lane];
+            atomicOr(&s_omask, 1 << ((kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2)));
+        }
+    }
+    __syncthreads();
+    const int om = s_omask, sh = D - d;
+    for (int x = tid; x < 8 * P; x += 32 * kChunkBoxes) {
+        const int o = x / P, n = x - (x / P) * P;
+        if (!((om >> o) & 1)) continue;
+        const float3 q = node_grid(gp, Ps, Pt, Pp, gam, n);
+        const float ox = (float)((2 * (o & 1) - 1) << sh);
+        const float oy = (float)((2 * ((o >> 1) & 1) - 1) << sh);
+        const float oz = (float)((2 * ((o >> 2) & 1) - 1) << sh);
+        s_alpha[o][n] = classify_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
+    }
+    __syncthreads();
+    if (warp >= nb) return;
+    for (int ch = 0; ch < nch; ++ch) {
+        const int4 kk = kd[k0 + ch];
+        const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
+        for (int n = lane; n < P; n += 32) mark.mark(k0 + ch, s_alpha[o][n]);
+    }
+}
+
 // Activation from the node tables: every node of every relevant parent cone marks the child
 // cone its table entry names (the same exact classification, computed once per gamma).
 __global__ void k_mark_parent_nodes_tab(int64_t ncp, const int32_t* __restrict__ pcone_box,
@@ -655,6 +735,48 @@ __global__ void k_dup_check(const double* __restrict__ Xs, int64_t N, const uint
 
 }  // namespace
 
+// Chunks of cones of one gamma (see k_gamma_keys) for a level without node tables. Boxes are
+// blocked so that a block of boxes holds about kChunkBoxes cones of each cone index, which
+// keeps the chunks full and the child cones of consecutive chunks close together. Chunks that
+// would hold fewer than two cones on average are not kept.
+void build_gamma_chunks(Plan& p, int dp) {
+    Level& Lp = p.L[dp];
+    Lp.n_gchunk = 0;
+    const int64_t nc = Lp.nc;
+    if (nc == 0) return;
+    const int C = Lp.g.C;
+    const double occ = (double)nc / ((double)Lp.n * (double)C);
+    int bb_shift = 4;
+    while (bb_shift < 30 && (double)((int64_t)1 << bb_shift) * occ < (double)kChunkBoxes) ++bb_shift;
+    const uint64_t maxkey = (uint64_t)(Lp.n >> bb_shift) * (uint64_t)C + (uint64_t)C;
+    int end_bit = 1;
+    while (end_bit < 64 && (maxkey >> end_bit) != 0) ++end_bit;
+    uint64_t* keys = dalloc<uint64_t>(p, (size_t)nc);
+    int32_t* order = dalloc<int32_t>(p, (size_t)nc);
+    IFGF_LAUNCH(k_gamma_keys, grid_for(nc, kThreads), kThreads, 0, p.stream, nc, Lp.cone_box, Lp.cone_gam, bb_shift,
+                C, keys, order);
+    radix_sort_pairs(p, keys, order, nc, end_bit);
+    int32_t* flags = dalloc<int32_t>(p, (size_t)nc);
+    int32_t* pos = dalloc<int32_t>(p, (size_t)nc);
+    IFGF_LAUNCH(k_gamma_chunk_flags, grid_for(nc, kThreads), kThreads, 0, p.stream, nc, keys, flags);
+    exclusive_scan_i32(p, flags, pos, nc);
+    const int64_t nchunk = (int64_t)read_one(p, pos + (nc - 1)) + read_one(p, flags + (nc - 1));
+    dfree_ptr(p, keys);
+    if ((double)nc < 2.0 * (double)nchunk) {
+        dfree_ptr(p, flags);
+        dfree_ptr(p, pos);
+        dfree_ptr(p, order);
+        return;
+    }
+    int32_t* gchunk = dalloc<int32_t>(p, (size_t)nchunk + 1);
+    IFGF_LAUNCH(k_gamma_chunk_fill, grid_for(nc, kThreads), kThreads, 0, p.stream, nc, flags, pos, gchunk);
+    dfree_ptr(p, flags);
+    dfree_ptr(p, pos);
+    Lp.gorder = order;
+    Lp.gchunk = gchunk;
+    Lp.n_gchunk = nchunk;
+}
+
 // Node tables of level dp (for its children at dp+1), when the cone indices are shared by
 // enough boxes and the tables stay small; otherwise the kernels compute the geometry.
 void build_node_tables(Plan& p, int dp) {
@@ -851,6 +973,9 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
                 if (Lp.nc > 0 && Lp.n_gam > 0)
                     IFGF_LAUNCH(k_mark_parent_nodes_tab, grid_for(Lp.nc * kTabList, kThreads), kThreads, 0, s, Lp.nc,
                                 Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, Lp.tab_k, Lp.tab_list, cm);
+                else if (Lp.nc > 0 && Lp.n_gchunk > 0)
+                    IFGF_LAUNCH(k_mark_parent_nodes_chunk, (unsigned)Lp.n_gchunk, 32 * kChunkBoxes, 0, s, Lp.gchunk,
+                                Lp.gorder, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, D, d, Lp.g, L.g, cm);
                 else if (Lp.nc > 0)
                     IFGF_LAUNCH(k_mark_parent_nodes, grid_for(Lp.nc * p.P, kThreads), kThreads, 0, s, Lp.nc, p.P, p.Ps,
                                 p.Pt, p.Pp, D, d, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, Lp.g, L.g, cm);
@@ -916,7 +1041,10 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
             IFGF_LAUNCH(k_box_cone_starts, grid_for((int64_t)L.n + 1, kThreads), kThreads, 0, s, L.n, L.nc, L.cone_box,
                         L.bcs);
         }
-        if (d < D && p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5) build_node_tables(p, d);
+        if (d < D && p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5) {
+            build_node_tables(p, d);
+            if (L.n_gam == 0) build_gamma_chunks(p, d);
+        }
         if (p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5 && p.max_nrhs >= 4) {
             int32_t* cnt = dalloc<int32_t>(p, L.n);
             int32_t* cpos2 = dalloc<int32_t>(p, L.n);
