@@ -181,6 +181,14 @@ const char* ifgf_last_error(void);
 int64_t ifgf_launch_count(void);
 
 /*
+ * Device memory of plans comes from one stream-ordered memory pool per device owned by this
+ * library; memory freed by ifgf_plan_destroy stays cached in the pool (up to a quarter of the
+ * device's memory) for the next plan.  This call returns every cached, unused byte of the pools
+ * to the device.  It synchronises each device that has a pool; plans remain valid.
+ */
+ifgf_status ifgf_release_cached_memory(void);
+
+/*
  * Opt-in live timing of the hot kernels: while enabled, every launch of a timed kernel is
  * bracketed by CUDA events on its own stream.  ifgf_timing_collect waits for the recorded
  * events, writes per-kind totals (milliseconds, launch counts) into ms[6] / launches[6]

@@ -135,6 +135,13 @@ def launch_count() -> int:
     return int(load().ifgf_launch_count())
 
 
+def release_cached_memory() -> None:
+    """Return the device memory cached by the library's memory pools (ifgf_release_cached_memory)."""
+    lib = load()
+    lib.ifgf_release_cached_memory.restype = ctypes.c_int
+    _check(lib.ifgf_release_cached_memory())
+
+
 def measure_peaks() -> dict:
     """Measured throughputs of the current device (separate probe library): FP32 FFMA and
     FP32x2 FFMA2 TFLOP/s, FP64 TFLOP/s, MUFU sine Gop/s, TF32 mma.sync TFLOP/s, SM count."""

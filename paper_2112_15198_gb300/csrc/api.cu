@@ -75,6 +75,38 @@ TimedScope::~TimedScope() {
     t.pending.emplace_back(kind, start, end);
 }
 
+namespace {
+std::mutex g_pool_mutex;
+std::vector<std::pair<int, cudaMemPool_t>> g_pools;
+}  // namespace
+
+cudaMemPool_t device_pool(int device) {
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    for (auto& e : g_pools)
+        if (e.first == device) return e.second;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    IFGF_CUDA(cudaMemPoolCreate(&pool, &props));
+    size_t free_b = 0, total_b = 0;
+    IFGF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    uint64_t keep = total_b / 4;
+    IFGF_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pools.emplace_back(device, pool);
+    return pool;
+}
+
+size_t pool_cached_bytes(int device) {
+    cudaMemPool_t pool = device_pool(device);
+    uint64_t reserved = 0, used = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 void destroy_plan(Plan& p) {
     for (size_t i = p.allocs.size(); i-- > 0;) cudaFreeAsync(p.allocs[i], p.stream);
     p.allocs.clear();
@@ -212,6 +244,7 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
         {
             size_t free_b = 0, total_b = 0;
             IFGF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            free_b += pool_cached_bytes(p->device);  // memory the pool holds for reuse
             const size_t io = 2 * (size_t)N * p->max_nrhs * csz + ((size_t)1 << 28);
             const size_t usable = free_b > io ? free_b - io : 0;
             int64_t M = layout_arena(*p, usable / 2);
@@ -476,6 +509,26 @@ void ifgf_timing_enable(int32_t on) {
     TimingState& t = timing();
     std::lock_guard<std::mutex> lk(t.mu);
     t.on = on != 0;
+}
+
+ifgf_status ifgf_release_cached_memory(void) {
+    std::vector<std::pair<int, cudaMemPool_t>> pools;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        pools = g_pools;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& e : pools) {
+        if (cudaSetDevice(e.first) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemPoolTrimTo(e.second, 0) != cudaSuccess) {
+            set_last_error(std::string("releasing cached memory: ") + cudaGetErrorString(cudaGetLastError()));
+            cudaSetDevice(cur);
+            return IFGF_ERR_CUDA;
+        }
+    }
+    cudaSetDevice(cur);
+    return IFGF_OK;
 }
 
 ifgf_status ifgf_timing_collect(double* ms, int64_t* launches) {

@@ -177,12 +177,25 @@ void set_last_error(const std::string& s);
 void cuda_check(cudaError_t e, const char* what);
 #define IFGF_CUDA(expr) ::ifgf::cuda_check((expr), #expr)
 
+// The library's stream-ordered memory pool of a device (created on first use; freed memory
+// stays cached up to a quarter of the device memory).
+cudaMemPool_t device_pool(int device);
+// Bytes the pool of a device holds but does not use (available to the next allocations).
+size_t pool_cached_bytes(int device);
+
 template <class T>
 T* dalloc(Plan& p, size_t count) {
     void* ptr = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(&ptr, bytes, p.stream);
+    cudaMemPool_t pool = device_pool(p.device);
+    cudaError_t e = cudaMallocFromPoolAsync(&ptr, bytes, pool, p.stream);
+    if (e != cudaSuccess) {  // return the pool's cached memory to the device and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(p.stream);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(&ptr, bytes, pool, p.stream);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(IFGF_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");

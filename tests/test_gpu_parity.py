@@ -321,3 +321,21 @@ def test_full_size_oblate128_many_densities():
     worst = max(oracle.rel_l2(got[r], exact[r]) for r in range(w.nrhs))
     print(f"oblate128 x 32: worst density rel. L2 error on {len(tgt)} targets = {worst:.3e}")
     assert worst < 5e-4
+
+
+def test_cached_memory_is_reused_and_released():
+    """Plan memory comes from the library's pool: a second plan of the same problem reuses the
+    cached memory, results are unchanged, and the cache can be returned to the device."""
+    pts = W.fibonacci_sphere(6000)
+    kappa = 2 * math.pi * 4
+    A = W.densities(6000, 1, 3)
+    first = _plan(pts, kappa)
+    a = _apply(first, A, "mixed")
+    first.destroy()
+    second = _plan(pts, kappa)
+    b = _apply(second, A, "mixed")
+    second.destroy()
+    np.testing.assert_array_equal(a, b)
+    ifgf.release_cached_memory()
+    third = _plan(pts, kappa)
+    np.testing.assert_array_equal(_apply(third, A, "mixed"), a)
