@@ -64,6 +64,10 @@ typedef enum {
  *               n_d x C_d table while it has fewer than 2^31 entries, else the sorted cone list
  *               searched per box), 1 always dense (IFGF_ERR_UNSUPPORTED beyond 2^31 entries),
  *               2 always the sorted list.  Results do not depend on the choice.
+ *   prop_slices the coefficients of consecutive levels share one buffer; propagation writes the
+ *               parent level in this many slices so that it never overwrites child coefficients
+ *               still to be read (0: one slice when two full levels fit the memory budget, else
+ *               64).  More slices need less memory and more launches; results do not change.
  */
 typedef struct {
     int32_t struct_size;   /* sizeof(ifgf_options) */
@@ -74,7 +78,7 @@ typedef struct {
     int32_t rhs_block;     /* densities per level sweep; 0 = as many as fit half the free memory */
     double tau;
     int32_t cone_table;    /* 0 automatic, 1 dense, 2 sorted list */
-    int32_t reserved;      /* must be 0 */
+    int32_t prop_slices;   /* 0 automatic, else propagation in this many slices (>= 1) */
 } ifgf_options;
 
 void ifgf_options_default(ifgf_options* opt);

@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
         ("rhs_block", ctypes.c_int32),
         ("tau", ctypes.c_double),
         ("cone_table", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("prop_slices", ctypes.c_int32),
     ]
 
 
@@ -178,7 +178,7 @@ class Plan:
 
     def __init__(self, points, kappa: float, orders=(3, 5, 5), levels: int = 0, precision: str = "mixed",
                  base_cones=(2, 4, 8), tau: float = 0.5, leaf_target: int = 64, max_nrhs: int = 1, stream=None,
-                 n: int | None = None, rhs_block: int = 0, cone_table: str = "auto"):
+                 n: int | None = None, rhs_block: int = 0, cone_table: str = "auto", prop_slices: int = 0):
         lib = load()
         self._lib = lib
         opt = Options()
@@ -190,6 +190,7 @@ class Plan:
         opt.max_nrhs = int(max_nrhs)
         opt.rhs_block = int(rhs_block)
         opt.cone_table = {"auto": 0, "dense": 1, "sorted": 2}[cone_table]
+        opt.prop_slices = int(prop_slices)
         if n is None:
             shape = tuple(points.shape)
             if len(shape) != 2 or shape[0] != 3:

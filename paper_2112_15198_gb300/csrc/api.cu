@@ -196,7 +196,7 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
     else if (opt.max_nrhs < 1 || opt.max_nrhs > 65535) why = "max_nrhs out of range";
     else if (opt.rhs_block < 0) why = "rhs_block must be >= 0";
     else if (opt.cone_table < 0 || opt.cone_table > 2) why = "cone_table must be 0, 1 or 2";
-    else if (opt.reserved != 0) why = "reserved must be 0";
+    else if (opt.prop_slices < 0 || opt.prop_slices > 4096) why = "prop_slices must be in [0, 4096]";
     else if (!(opt.tau > 0.0) || !std::isfinite(opt.tau)) why = "tau must be finite and > 0";
     else if (!((Ps == 3 && Pt == 5 && Pp == 5) || (Ps == 5 && Pt == 7 && Pp == 7)))
         why = "orders must be (3,5,5) or (5,7,7) in this build";
@@ -247,11 +247,11 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
             free_b += pool_cached_bytes(p->device);  // memory the pool holds for reuse
             const size_t io = 2 * (size_t)N * p->max_nrhs * csz + ((size_t)1 << 28);
             const size_t usable = free_b > io ? free_b - io : 0;
-            int64_t M = layout_arena(*p, usable / 2);
+            int64_t M = layout_arena(*p, usable / 2, opt.prop_slices);
             size_t budget = usable / 2;
             if (M == 0) {
                 budget = usable / 10 * 9;
-                M = layout_arena(*p, budget);
+                M = layout_arena(*p, budget, opt.prop_slices);
             }
             if (M == 0) fail(IFGF_ERR_OOM, "the coefficient arena of one density does not fit in device memory");
             p->arena_cones = M;

@@ -256,8 +256,8 @@ void radix_sort_pairs(Plan& p, uint64_t* keys, int32_t* vals, int64_t n, int end
 void build_plan(Plan& p, const double* points, const ifgf_options& opt, int levels);
 // Coefficient arena layout: slices per level and arena size for at most `budget` bytes per
 // density (cone blocks of cstride complex values); returns the arena size in cones, 0 if the
-// levels cannot be laid out in the budget.
-int64_t layout_arena(Plan& p, size_t budget_per_rhs);
+// levels cannot be laid out in the budget. slices = 0: one slice if it fits, else 64.
+int64_t layout_arena(Plan& p, size_t budget_per_rhs, int slices);
 // Level d's first cone block in the arena for blocks of nb densities.
 inline char* level_coef(const Plan& p, int d, int nb) {
     const size_t csz = p.precision == IFGF_PREC_MIXED ? 8 : 16;

@@ -1109,8 +1109,12 @@ static int64_t arena_for_slices(Plan& p, int k) {
     return std::max<int64_t>(M, 1);
 }
 
-int64_t layout_arena(Plan& p, size_t budget_per_rhs) {
+int64_t layout_arena(Plan& p, size_t budget_per_rhs, int slices) {
     const size_t cone = (size_t)p.cstride * (p.precision == IFGF_PREC_MIXED ? 8 : 16);
+    if (slices > 0) {
+        const int64_t Mk = arena_for_slices(p, slices);
+        return (size_t)Mk * cone <= budget_per_rhs ? Mk : 0;
+    }
     int64_t M = arena_for_slices(p, 1);  // one launch per level: two full levels
     if ((size_t)M * cone <= budget_per_rhs) return M;
     M = arena_for_slices(p, 64);

@@ -339,3 +339,22 @@ def test_cached_memory_is_reused_and_released():
     ifgf.release_cached_memory()
     third = _plan(pts, kappa)
     np.testing.assert_array_equal(_apply(third, A, "mixed"), a)
+
+
+@pytest.mark.parametrize("prec,nrhs,cone_table", [("mixed", 1, "auto"), ("fp64", 1, "auto"), ("mixed", 8, "auto"),
+                                                   ("mixed", 1, "sorted")])
+def test_sliced_propagation_equals_one_slice(prec, nrhs, cone_table):
+    """Propagation in many slices (consecutive levels at opposite ends of one coefficient buffer,
+    slices ordered so no child coefficient is overwritten before it is read) gives bit-identical
+    results to one slice per level."""
+    pts = W.spheroid(15_000, 0.5, 0.2, seed=44)
+    kappa = 2 * math.pi * 7
+    A = W.densities(pts.shape[1], nrhs, 45)
+    one = _plan(pts, kappa, precision=prec, max_nrhs=nrhs, prop_slices=1, cone_table=cone_table)
+    many = _plan(pts, kappa, precision=prec, max_nrhs=nrhs, prop_slices=37, cone_table=cone_table)
+    a = _apply(one, A, prec)
+    b = _apply(many, A, prec)
+    assert one.status() == 0 and many.status() == 0
+    np.testing.assert_array_equal(a, b)
+    ref = oracle.Plan(pts, kappa).apply(A)
+    assert oracle.rel_l2(b, ref) < (1e-10 if prec == "fp64" else 3e-5)
