@@ -130,7 +130,20 @@ WORKLOADS = {
     # 512-wavelength sphere; the Laplace repeat uses wavelengths = 0.
     "sphere512": Workload("sphere512", "sphere", 25_165_824, 512.0, 1, 5, 2000),
     "sphere512_laplace": Workload("sphere512_laplace", "sphere", 25_165_824, 0.0, 1, 5, 2000),
+    # Prolate spheroid (a, a, 10a) of unit length, the paper's third geometry.
+    "prolate128": Workload("prolate128", "spheroid", 6_291_456, 128.0, 1, 7, 2000, (0.05, 0.5)),
 }
+
+
+def linearithmic_series(geometry: str = "sphere") -> list:
+    """Four problems at a fixed sampling density (about 122 points per square wavelength on the
+    sphere): each doubles the wavelengths across the body and quadruples N, from 393,216 points
+    at 32 wavelengths to 25,165,824 at 256 (sphere; the prolate spheroid (a, a, 10a) keeps the same
+    N and its length in wavelengths)."""
+    axes = (0.5, 0.5) if geometry == "sphere" else (0.05, 0.5)
+    return [Workload(f"{geometry}_n{n}", geometry, n, lam, 1, 11 + i, 200, axes)
+            for i, (n, lam) in enumerate(((393_216, 32.0), (1_572_864, 64.0), (6_291_456, 128.0),
+                                          (25_165_824, 256.0)))]
 
 
 def make(name: str) -> Workload:
