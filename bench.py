@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--workload", default="sphere64")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
 
@@ -178,7 +178,8 @@ def run_reference(args, ws, rank):
     dens = w.densities()
     threads = oracle.max_threads()
     # bounded sample: enough targets for ~3 s of CPU work per step
-    probe = W.targets(w.n, 32, 999)
+    probe = W.targets(w.n, 64, 999)
+    oracle.direct_sum(pts, w.kappa, dens, probe[:4])  # thread pool start-up, untimed
     t0 = time.perf_counter()
     oracle.direct_sum(pts, w.kappa, dens, probe)
     per_target = (time.perf_counter() - t0) / len(probe)
@@ -372,7 +373,8 @@ def main():
 
         oracle.build()
         threads = oracle.max_threads()
-        probe = W.targets(w.n, 32, 999)
+        probe = W.targets(w.n, 64, 999)
+        oracle.direct_sum(pts, w.kappa, dens_np, probe[:4])  # thread pool start-up, untimed
         t0 = time.perf_counter()
         oracle.direct_sum(pts, w.kappa, dens_np, probe)
         per_target = (time.perf_counter() - t0) / len(probe)
