@@ -1128,116 +1128,6 @@ k_prop_mma_tab(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
     }
 }
 
-// Interpolation with many densities: one warp per chunk of <= 16 targets of one level-d box (the
-// chunks are built by the plan); for every cousin box, an MMA block per distinct cone.
-template <int PS, int PT, int PP, int NT>
-__global__ void __launch_bounds__(128)
-k_interp_mma(int64_t nchunk, const int32_t* __restrict__ chunk_box, const int32_t* __restrict__ chunk_start,
-             const int32_t* __restrict__ start_d, int64_t N, int sh, const int32_t* __restrict__ pbox_D,
-             const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
-             const int32_t* __restrict__ cs, const float4* __restrict__ off, ConeMap cm,
-             LevelGrid g, const float2* __restrict__ coef, const float* __restrict__ phtab, float ku, float inv4piu,
-             float2* __restrict__ Is, int cstride, int nrhs, int* __restrict__ status) {
-    const int64_t ch = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (ch >= nchunk) return;  // whole warp leaves together
-    constexpr int NR = 4 * NT;
-    const int rhs0 = blockIdx.y * NR;
-    const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
-    const int A = chunk_box[ch];
-    const int i0 = chunk_start[ch];
-    const int iend = start_d[A + 1];
-    const int t0 = i0 + gq, t1 = t0 + 8;
-    const bool v0 = t0 < iend, v1 = t1 < iend;
-    const int4 kA = kd[A];
-    const float cscale = (float)(2 << sh);
-    struct Tgt {
-        int4 kl;
-        float4 o;
-        float dax, day, daz, dd;
-    };
-    auto tgt = [&](int i) -> Tgt {
-        Tgt T;
-        T.kl = kD[pbox_D[i]];
-        T.o = off[i];
-        T.dax = (float)((2 * T.kl.x + 1) - ((2 * kA.x + 1) << sh)) + T.o.x;
-        T.day = (float)((2 * T.kl.y + 1) - ((2 * kA.y + 1) << sh)) + T.o.y;
-        T.daz = (float)((2 * T.kl.z + 1) - ((2 * kA.z + 1) << sh)) + T.o.z;
-        T.dd = fmaf(T.dax, T.dax, fmaf(T.day, T.day, T.daz * T.daz));
-        return T;
-    };
-    const Tgt T0 = tgt(v0 ? t0 : i0), T1 = tgt(v1 ? t1 : i0);
-    float acc[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const int nc = ncs[A];
-    for (int tc = 0; tc < nc; ++tc) {
-        const int B = cs[(int64_t)A * kMaxCous + tc];
-        const int4 kb = kd[B];
-        const int nx = kA.x - kb.x, ny = kA.y - kb.y, nz = kA.z - kb.z;
-        const int nn = nx * nx + ny * ny + nz * nz;
-        const float cx = cscale * nx, cy = cscale * ny, cz = cscale * nz;
-        const float cn = cscale * sqrtf((float)nn);
-        const float ph0 = __ldg(&phtab[nn]);
-        auto loc = [&](const Tgt& T) -> ConeLocal {
-            const float vx = __fadd_rn((float)((2 * T.kl.x + 1) - ((2 * kb.x + 1) << sh)), T.o.x);
-            const float vy = __fadd_rn((float)((2 * T.kl.y + 1) - ((2 * kb.y + 1) << sh)), T.o.y);
-            const float vz = __fadd_rn((float)((2 * T.kl.z + 1) - ((2 * kb.z + 1) << sh)), T.o.z);
-            return locate_f32(g, vx, vy, vz);
-        };
-        auto green = [&](const Tgt& T, const ConeLocal& cl) -> float2 {
-            const float num = fmaf(2.f, fmaf(cx, T.dax, fmaf(cy, T.day, cz * T.daz)), T.dd);
-            const float corr = __fdividef(num, cl.r + cn);
-            const float2 e = cis_f32(fmaf(ku, corr, ph0));
-            const float w = __fdividef(inv4piu, cl.r);
-            return make_float2(e.x * w, e.y * w);
-        };
-        const ConeLocal c0 = loc(T0), c1 = loc(T1);
-        const float2 G0 = green(T0, c0), G1 = green(T1, c1);
-        float Ts0[PS], Tt0[PT], Tp0[PP], Ts1[PS], Tt1[PT], Tp1[PP];
-        cheb_T<PS>(c0.ts, Ts0);
-        cheb_T<PT>(c0.tt, Tt0);
-        cheb_T<PP>(c0.tp, Tp0);
-        cheb_T<PS>(c1.ts, Ts1);
-        cheb_T<PT>(c1.tt, Tt1);
-        cheb_T<PP>(c1.tp, Tp1);
-        for_each_cone(c0.gamma(g), c1.gamma(g), v0, v1, [&](int alpha, bool m0, bool m1) {
-            const int s = cm.find(B, alpha);
-            if (s < 0) {
-                if (m0 || m1) set_status(status, IFGF_ERR_INTERNAL);
-                return;
-            }
-            float c[NT][4];
-#pragma unroll
-            for (int j = 0; j < NT; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.f;
-            mma_interp_block<PS, PT, PP, NT>(Ts0, Tt0, Tp0, Ts1, Tt1, Tp1, m0, m1, coef, s, nrhs, rhs0, cstride, c);
-#pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                if (m0) {
-                    acc[j][0] += G0.x * c[j][0] - G0.y * c[j][1];
-                    acc[j][1] += G0.x * c[j][1] + G0.y * c[j][0];
-                }
-                if (m1) {
-                    acc[j][2] += G1.x * c[j][2] - G1.y * c[j][3];
-                    acc[j][3] += G1.x * c[j][3] + G1.y * c[j][2];
-                }
-            }
-        });
-    }
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        const int rhs = rhs0 + j * 4 + tq;
-        if (rhs >= nrhs) continue;
-        if (v0) {
-            float2* d = Is + (int64_t)rhs * N + t0;
-            *d = make_float2(d->x + acc[j][0], d->y + acc[j][1]);
-        }
-        if (v1) {
-            float2* d = Is + (int64_t)rhs * N + t1;
-            *d = make_float2(d->x + acc[j][2], d->y + acc[j][3]);
-        }
-    }
-}
-
 // Near field and leaf evaluation with a block of NR densities: the kernel value of each pair is
 // computed once and applied to every density of the block.
 template <int NR>
@@ -1430,11 +1320,11 @@ void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStre
     for (int d = D; d >= 3; --d) {
         Level& L = p.L[d];
         const int sh = D - d;
-        if (((mask >> d) & 1) && L.nchunk > 0) {
+        if ((mask >> d) & 1) {
             TimedScope ts_(TK_INTERP, s);
-            IFGF_LAUNCH((k_interp_mma<PS, PT, PP, NT>), dim3((unsigned)((L.nchunk + 3) / 4), rb), 128, 0, s, L.nchunk,
-                        L.chunk_box, L.chunk_start, L.start, N, sh, LD.pbox, LD.k, L.k, L.ncs, L.cs, p.off, L.cmap(), L.g,
-                        (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status);
+            IFGF_LAUNCH((k_interp_f32<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs, L.cs,
+                        p.off, L.cmap(), L.g, (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu, Is,
+                        p.cstride, nrhs, p.d_status);
         }
         if (d == 3) break;
         Level& Lp = p.L[d - 1];

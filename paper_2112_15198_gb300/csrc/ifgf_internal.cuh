@@ -123,10 +123,6 @@ struct Level {
     int64_t n_gchunk = 0;
     int32_t* gorder = nullptr;     // [nc]
     int32_t* gchunk = nullptr;     // [n_gchunk+1]
-    // Target chunks of <= 16 points of one box (tensor-core interpolation with many densities).
-    int64_t nchunk = 0;
-    int32_t* chunk_box = nullptr;
-    int32_t* chunk_start = nullptr;
     // Propagation into this level (as the parent level): cone boundaries of its slices.
     std::vector<int64_t> pslice;
 };

@@ -558,21 +558,6 @@ __global__ void k_mark_parent_nodes_tab(int64_t ncp, const int32_t* __restrict__
     }
 }
 
-// Chunks of at most 16 consecutive targets of one box (per-box counts, then the chunk list).
-__global__ void k_chunk_count(const int32_t* __restrict__ start, int n, int32_t* __restrict__ cnt) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < n) cnt[b] = (start[b + 1] - start[b] + 15) / 16;
-}
-__global__ void k_chunk_fill(const int32_t* __restrict__ start, int n, const int32_t* __restrict__ pos,
-                             int32_t* __restrict__ chunk_box, int32_t* __restrict__ chunk_start) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-    int c = pos[b];
-    for (int i = start[b]; i < start[b + 1]; i += 16, ++c) {
-        chunk_box[c] = b;
-        chunk_start[c] = i;
-    }
-}
 
 // Sparse levels: the hash set's keys become the cone list sorted by (box, gamma).
 __global__ void k_hash_flags(int64_t H, const unsigned long long* __restrict__ hkeys, int32_t* __restrict__ flags) {
@@ -1044,19 +1029,6 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
         if (d < D && p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5) {
             build_node_tables(p, d);
             if (L.n_gam == 0) build_gamma_chunks(p, d);
-        }
-        if (p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5 && p.max_nrhs >= 4) {
-            int32_t* cnt = dalloc<int32_t>(p, L.n);
-            int32_t* cpos2 = dalloc<int32_t>(p, L.n);
-            IFGF_LAUNCH(k_chunk_count, grid_for(L.n, kThreads), kThreads, 0, s, L.start, L.n, cnt);
-            exclusive_scan_i32(p, cnt, cpos2, L.n);
-            L.nchunk = (int64_t)read_one(p, cpos2 + (L.n - 1)) + read_one(p, cnt + (L.n - 1));
-            L.chunk_box = dalloc<int32_t>(p, L.nchunk);
-            L.chunk_start = dalloc<int32_t>(p, L.nchunk);
-            IFGF_LAUNCH(k_chunk_fill, grid_for(L.n, kThreads), kThreads, 0, s, L.start, L.n, cpos2, L.chunk_box,
-                        L.chunk_start);
-            dfree_ptr(p, cnt);
-            dfree_ptr(p, cpos2);
         }
     }
 }
