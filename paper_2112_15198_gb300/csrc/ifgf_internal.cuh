@@ -566,42 +566,6 @@ __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, con
     }
 }
 
-// The same contraction for a coefficient block staged in shared memory (P_phi = 5 layout:
-// 16-byte aligned block, two rows per five 128-bit loads).
-template <int PS, int PT>
-__device__ __forceinline__ float2 interp_f32_smem(const float4* c4, float ts, float tt, float tp) {
-    constexpr int PP = 5;
-    float Ts[PS], Tt[PT], Tp[PP];
-    cheb_T<PS>(ts, Ts);
-    cheb_T<PT>(tt, Tt);
-    cheb_T<PP>(tp, Tp);
-    constexpr int R = PS * PT;
-    float2 aa[PS];
-#pragma unroll
-    for (int a = 0; a < PS; ++a) aa[a] = make_float2(0.f, 0.f);
-    auto fold = [&](int rr, float2 row) {
-        const int a = rr / PT, b = rr - (rr / PT) * PT;
-        aa[a] = __ffma2_rn(row, make_float2(Tt[b], Tt[b]), aa[a]);
-    };
-#pragma unroll
-    for (int m = 0; m < R / 2; ++m) {
-        const float4 v0 = c4[5 * m + 0], v1 = c4[5 * m + 1], v2 = c4[5 * m + 2], v3 = c4[5 * m + 3], v4 = c4[5 * m + 4];
-        fold(2 * m, row5(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
-                         make_float2(v1.z, v1.w), make_float2(v2.x, v2.y), Tp));
-        fold(2 * m + 1, row5(make_float2(v2.z, v2.w), make_float2(v3.x, v3.y), make_float2(v3.z, v3.w),
-                             make_float2(v4.x, v4.y), make_float2(v4.z, v4.w), Tp));
-    }
-    if constexpr (R % 2 == 1) {
-        const float4 v0 = c4[5 * (R / 2) + 0], v1 = c4[5 * (R / 2) + 1], v2 = c4[5 * (R / 2) + 2];
-        fold(R - 1, row5(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
-                         make_float2(v1.z, v1.w), make_float2(v2.x, v2.y), Tp));
-    }
-    float2 acc = aa[0];
-#pragma unroll
-    for (int a = 1; a < PS; ++a) acc = __ffma2_rn(aa[a], make_float2(Ts[a], Ts[a]), acc);
-    return acc;
-}
-
 template <int PS, int PT, int PP>
 __device__ __forceinline__ double2 interp_f64(const double2* __restrict__ c, double ts, double tt, double tp) {
     double Ts[PS], Tt[PT], Tp[PP];
