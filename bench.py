@@ -38,7 +38,7 @@ UNIT = "pts/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic FP32 flops per unit of work (counted from the arithmetic of the method's
-# steps, independent of how the kernels schedule it; derivation in the design doc):
+# steps, independent of how the kernels schedule it):
 #   interpolant evaluation at one point, orders (3,5,5): separable contraction
 #   4*(75+15+3) = 372, Chebyshev recurrences 2*(1+3+3) = 14, local coordinates 6,
 #   squared distance 5, factor/ratio multiply-accumulate 18  -> 415

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances:
   - tree, interaction lists, cone lists: bit-exact (integer work);
   - FP64 path vs CPU IFGF (same algorithm, FP64, different summation order): rel. L2 1e-10;
   - mixed path vs CPU IFGF: rel. L2 3e-5 (FP32 arithmetic over D levels of interpolation);
