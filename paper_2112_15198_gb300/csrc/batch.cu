@@ -1,10 +1,12 @@
 // Batched apply: many plans evaluated as one CUDA-graph launch sequence.
 //
-// The first ifgf_batch_apply with a given set of buffers captures the apply of every plan, in
-// order, on a private stream into a CUDA graph; later calls with the same buffers replay it
-// with one cudaGraphLaunch on the caller's stream (different buffers trigger a new capture).
+// The first ifgf_batch_apply with a given set of buffers captures the apply of every plan on
+// private streams into a CUDA graph (problem i on branch i mod 8 of a fork/join, so independent
+// problems run concurrently); later calls with the same buffers replay it with one
+// cudaGraphLaunch on the caller's stream (different buffers trigger a new capture).
 // The problems of the batch share the launch sequence, not their data: each plan keeps its
 // own tree, cones and scratch.
+#include <algorithm>
 #include <functional>
 #include <string>
 #include <vector>
@@ -17,6 +19,10 @@ struct ifgf_batch_s {
     std::vector<ifgf::Plan*> plans;
     int device = 0;
     cudaStream_t cap = nullptr;
+    // independent problems run on kBranches concurrent branches of the graph (captured on
+    // forked streams), so that small problems fill the GPU together
+    std::vector<cudaStream_t> branch;
+    std::vector<cudaEvent_t> ev;  // fork event, then one join event per branch
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> dens;
@@ -33,6 +39,7 @@ ifgf_status guard_call(const std::function<void()>& f);
 using namespace ifgf;
 
 namespace {
+constexpr int kBranches = 8;
 void drop_graph(ifgf_batch_s& b) {
     if (b.exec) cudaGraphExecDestroy(b.exec);
     if (b.graph) cudaGraphDestroy(b.graph);
@@ -61,8 +68,21 @@ ifgf_status ifgf_batch_create(const ifgf_plan* plans, int32_t n, ifgf_batch* out
             if (p->device != b->device) fail(IFGF_ERR_INVALID_ARG, "plans of a batch must share one device");
         IFGF_CUDA(cudaSetDevice(b->device));
         IFGF_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        const int nb = (int)std::min<size_t>(kBranches, b->plans.size());
+        for (int i = 0; i < nb; ++i) {
+            cudaStream_t st2 = nullptr;
+            IFGF_CUDA(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+            b->branch.push_back(st2);
+        }
+        for (int i = 0; i <= nb; ++i) {
+            cudaEvent_t e = nullptr;
+            IFGF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            b->ev.push_back(e);
+        }
     });
     if (st != IFGF_OK) {
+        for (cudaStream_t x : b->branch) cudaStreamDestroy(x);
+        for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
         if (b->cap) cudaStreamDestroy(b->cap);
         delete b;
         return st;
@@ -98,8 +118,17 @@ ifgf_status ifgf_batch_apply(ifgf_batch b, const void* const* dens, const int32_
             const int64_t l0 = g_launches.load();
             IFGF_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
             try {
+                // fork: every branch waits for the capture stream, runs every kb-th problem in order,
+                // and the capture stream joins all branches
+                const size_t kb = b->branch.size();
+                IFGF_CUDA(cudaEventRecord(b->ev[0], b->cap));
+                for (size_t j = 0; j < kb; ++j) IFGF_CUDA(cudaStreamWaitEvent(b->branch[j], b->ev[0], 0));
                 for (size_t i = 0; i < n; ++i)
-                    apply_plan(*b->plans[i], dens[i], nrhs[i], outs[i], b->cap, true, -1);
+                    apply_plan(*b->plans[i], dens[i], nrhs[i], outs[i], b->branch[i % kb], true, -1);
+                for (size_t j = 0; j < kb; ++j) {
+                    IFGF_CUDA(cudaEventRecord(b->ev[j + 1], b->branch[j]));
+                    IFGF_CUDA(cudaStreamWaitEvent(b->cap, b->ev[j + 1], 0));
+                }
             } catch (...) {
                 cudaGraph_t g = nullptr;
                 cudaStreamEndCapture(b->cap, &g);
@@ -124,6 +153,8 @@ ifgf_status ifgf_batch_destroy(ifgf_batch b) {
     if (!b) return IFGF_OK;
     cudaSetDevice(b->device);
     drop_graph(*b);
+    for (cudaStream_t x : b->branch) cudaStreamDestroy(x);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
     return IFGF_OK;
