@@ -544,18 +544,20 @@ __global__ void k_mark_parent_nodes_tab(int64_t ncp, const int32_t* __restrict__
                                         const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
                                         const int32_t* __restrict__ tab_k, const int32_t* __restrict__ tab_list,
                                         ConeMark mark) {
+    // one thread per (parent cone, child slot): the row's distinct child cones are marked in the child
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ncp * kTabList) return;
-    const int64_t pc = t / kTabList;
-    const int k = (int)(t - pc * kTabList);
+    if (t >= ncp * 8) return;
+    const int64_t pc = t >> 3;
+    const int ch = (int)(t & 7);
     const int jb = pcone_box[pc];
-    const int64_t row = (int64_t)cone_gidx[pc] * 8;
+    const int kb = pcstart[jb] + ch;
+    if (kb >= pcstart[jb + 1]) return;
     const int4 kj = kp[jb];
-    for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
-        const int4 kk = kd[kb];
-        const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
-        if (k < tab_k[row + o]) mark.mark(kb, tab_list[(row + o) * kTabList + k]);
-    }
+    const int4 kk = kd[kb];
+    const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
+    const int64_t row = (int64_t)cone_gidx[pc] * 8 + o;
+    const int K = tab_k[row];
+    for (int k = 0; k < K; ++k) mark.mark(kb, tab_list[row * kTabList + k]);
 }
 
 
@@ -956,7 +958,7 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
             if (d > 3) {
                 Level& Lp = p.L[d - 1];
                 if (Lp.nc > 0 && Lp.n_gam > 0)
-                    IFGF_LAUNCH(k_mark_parent_nodes_tab, grid_for(Lp.nc * kTabList, kThreads), kThreads, 0, s, Lp.nc,
+                    IFGF_LAUNCH(k_mark_parent_nodes_tab, grid_for(Lp.nc * 8, kThreads), kThreads, 0, s, Lp.nc,
                                 Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, Lp.tab_k, Lp.tab_list, cm);
                 else if (Lp.nc > 0 && Lp.n_gchunk > 0)
                     IFGF_LAUNCH(k_mark_parent_nodes_chunk, (unsigned)Lp.n_gchunk, 32 * kChunkBoxes, 0, s, Lp.gchunk,
