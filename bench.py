@@ -335,7 +335,7 @@ def main():
     per_launch_flops = flops[dom] * args.steps / dom_n
     achieved = per_launch_flops / (dom_ms / dom_n / 1e3) / 1e12
     kernel_name = {"prop": "k_prop_warp_f32" if args.precision == "mixed" else "k_prop_f64",
-                   "interp": "k_interp_f32", "leaf": "k_leaf_box_f32", "near": "k_near_f32"}[dom]
+                   "interp": "k_interp_f32", "leaf": "k_leaf_box_f32", "near": "k_near_tile_f32"}[dom]
     # FP32 (FP64) FMA throughput measured on this device by the probe kernels
     try:
         peaks = ifgf.measure_peaks()

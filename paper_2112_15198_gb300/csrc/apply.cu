@@ -35,43 +35,77 @@ __global__ void k_perm_out(const T* __restrict__ Is, const int32_t* __restrict__
     out[r * N + perm[i]] = Is[r * N + i];
 }
 
+
 // ---- near field --------------------------------------------------------------------------
 // I(x_l) = sum over the points x_m of the 27 neighbour leaves of leaf(x_l), m != l, of a_m G.
-__global__ void k_near_f32(int64_t N, const int32_t* __restrict__ pboxD, const int4* __restrict__ kD,
-                           const int32_t* __restrict__ startD, const int32_t* __restrict__ nnb,
-                           const int32_t* __restrict__ nb, const float4* __restrict__ off,
-                           const float2* __restrict__ as, float2* __restrict__ Is, float ku, float inv4piu) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+
+// Near field with one block per leaf box (the paper's LevelDSingularInteractions): the sources of
+// the box's neighbourhood are staged in shared memory in tiles of kNearTile (coalesced 128-bit
+// offset and 64-bit density loads), each shifted once to the target box's frame. With m targets
+// in the box, S = 2^k <= min(32, kNearThreads / m) threads share a target and take every S-th
+// source of a tile; their partial sums are combined by warp shuffles in a fixed order.
+constexpr int kNearThreads = 128;
+constexpr int kNearTile = 128;
+__global__ void __launch_bounds__(kNearThreads)
+k_near_tile_f32(const int4* __restrict__ kD, const int32_t* __restrict__ startD, const int32_t* __restrict__ nnb,
+                const int32_t* __restrict__ nb, const float4* __restrict__ off, const float2* __restrict__ as,
+                float2* __restrict__ Is, int64_t N, float ku, float inv4piu) {
+    __shared__ float4 s_p[kNearTile];  // source position in the target box's grid frame; w = source index
+    __shared__ float2 s_a[kNearTile];
+    const int l = blockIdx.x;
     const int64_t r = blockIdx.y;
-    const int l = pboxD[i];
+    const int tid = threadIdx.x;
+    const int t0 = startD[l], m = startD[l + 1] - t0;
     const int4 kl = kD[l];
-    const float4 oi = off[i];
     const float2* ar = as + r * N;
-    float2 acc = make_float2(0.f, 0.f);
+    int S = 1;
+    while (S < 32 && 2 * S * m <= kNearThreads) S *= 2;
+    const int per_pass = kNearThreads / S;  // targets per pass
     const int cnt = nnb[l];
-    for (int t = 0; t < cnt; ++t) {
-        const int q = nb[(int64_t)l * kMaxNbr + t];
-        const int4 kq = kD[q];
-        const float bx = (float)(2 * (kl.x - kq.x)) + oi.x;
-        const float by = (float)(2 * (kl.y - kq.y)) + oi.y;
-        const float bz = (float)(2 * (kl.z - kq.z)) + oi.z;
-        const int j1 = startD[q + 1];
-        for (int j = startD[q]; j < j1; ++j) {
-            if (j == i) continue;
-            const float4 oj = __ldg(&off[j]);
-            const float vx = bx - oj.x, vy = by - oj.y, vz = bz - oj.z;
-            const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-            const float rinv = rsqrtf(r2);
-            const float2 e = cis_f32(ku * (r2 * rinv));
-            const float w = inv4piu * rinv;
-            const float2 aj = __ldg(&ar[j]);
-            const float2 g = make_float2(e.x * w, e.y * w);
-            acc = __ffma2_rn(make_float2(aj.x, aj.x), g, acc);
-            acc = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(g.y, g.x), acc);
+    for (int base = 0; base < m; base += per_pass) {
+        const int tl = base + tid / S, part = tid % S;
+        const bool active = tl < m;
+        const int i = t0 + (active ? tl : 0);
+        const float4 oi = off[i];
+        float2 acc = make_float2(0.f, 0.f);
+        for (int nq = 0; nq < cnt; ++nq) {
+            const int q = nb[(int64_t)l * kMaxNbr + nq];
+            const int4 kq = kD[q];
+            const float sx = (float)(2 * (kl.x - kq.x)), sy = (float)(2 * (kl.y - kq.y)),
+                        sz = (float)(2 * (kl.z - kq.z));
+            const int j0 = startD[q], j1 = startD[q + 1];
+            for (int tb = j0; tb < j1; tb += kNearTile) {
+                const int nt = min(kNearTile, j1 - tb);
+                __syncthreads();
+                if (tid < nt) {
+                    const float4 oj = __ldg(&off[tb + tid]);
+                    s_p[tid] = make_float4(oj.x - sx, oj.y - sy, oj.z - sz, __int_as_float(tb + tid));
+                    s_a[tid] = __ldg(&ar[tb + tid]);
+                }
+                __syncthreads();
+                if (active) {
+                    for (int k = part; k < nt; k += S) {
+                        const float4 pj = s_p[k];
+                        if (__float_as_int(pj.w) == i) continue;
+                        const float vx = oi.x - pj.x, vy = oi.y - pj.y, vz = oi.z - pj.z;
+                        const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+                        const float rinv = rsqrtf(r2);
+                        const float2 e = cis_f32(ku * (r2 * rinv));
+                        const float w = inv4piu * rinv;
+                        const float2 aj = s_a[k];
+                        const float2 g = make_float2(e.x * w, e.y * w);
+                        acc = __ffma2_rn(make_float2(aj.x, aj.x), g, acc);
+                        acc = __ffma2_rn(make_float2(-aj.y, aj.y), make_float2(g.y, g.x), acc);
+                    }
+                }
+            }
         }
+        for (int o = S / 2; o >= 1; o >>= 1) {  // the S partial sums of a target, fixed order
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (active && part == 0) Is[r * N + i] = acc;
     }
-    Is[r * N + i] = acc;
 }
 
 __global__ void k_near_f64(int64_t N, const int32_t* __restrict__ pboxD, const int32_t* __restrict__ startD,
@@ -1392,8 +1426,8 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
         if (near)
             {
                 TimedScope ts_(TK_NEAR, s);
-                IFGF_LAUNCH(k_near_f32, gN, kThreads, 0, s, N, LD.pbox, LD.k, LD.start, LD.nnb, LD.nb, p.off, as, Is, ku,
-                            inv4piu);
+                IFGF_LAUNCH(k_near_tile_f32, dim3((unsigned)LD.n, nrhs), kNearThreads, 0, s, LD.k, LD.start, LD.nnb,
+                            LD.nb, p.off, as, Is, N, ku, inv4piu);
             }
         else
             IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * nrhs, s));
