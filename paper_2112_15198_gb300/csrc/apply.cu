@@ -35,7 +35,6 @@ __global__ void k_perm_out(const T* __restrict__ Is, const int32_t* __restrict__
     out[r * N + perm[i]] = Is[r * N + i];
 }
 
-
 // ---- near field --------------------------------------------------------------------------
 // I(x_l) = sum over the points x_m of the 27 neighbour leaves of leaf(x_l), m != l, of a_m G.
 
