@@ -748,7 +748,7 @@ __global__ void k_prop_f64(const int32_t* __restrict__ pcone_box, const int32_t*
 // integer centre offset c_A - c_k = 2^(D-d+1) n, so
 //   kappa |x - x_k| = (kappa H_d sqrt(|n|^2) mod 2 pi) + kappa u (2 c.d_A + |d_A|^2)/(|x - x_k| + |c|).
 template <int PS, int PT, int PP>
-__global__ void k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
+__global__ void __launch_bounds__(kThreads, 5) k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
                              const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
                              const int32_t* __restrict__ cs, const float4* __restrict__ off,
                              ConeMap cm, LevelGrid g, const float2* __restrict__ coef,
