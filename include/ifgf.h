@@ -57,9 +57,10 @@ typedef enum {
  *   leaf_target when levels == 0, D is the smallest level >= 3 whose mean relevant-leaf
  *               occupancy N / n_D is at most leaf_target.
  *   max_nrhs    largest nrhs that ifgf_apply will accept (buffers are sized for it).
- *   rhs_block   the coefficient buffers hold this many densities; ifgf_apply sweeps the levels
- *               once per block of densities (0: the largest block, up to max_nrhs, whose two
- *               coefficient buffers fit in half the free device memory at plan time).
+ *   rhs_block   the coefficient buffer holds this many densities; ifgf_apply sweeps the levels
+ *               once per block of densities (0: the largest block, up to max_nrhs, whose
+ *               coefficients fit in half the free device memory at plan time, or in 90% of it
+ *               when not even one density fits in half).
  *   cone_table  how a level finds the relevant cone of (box, cone index): 0 automatic (a dense
  *               n_d x C_d table while it has fewer than 2^31 entries, else the sorted cone list
  *               searched per box), 1 always dense (IFGF_ERR_UNSUPPORTED beyond 2^31 entries),
@@ -102,7 +103,8 @@ void ifgf_options_default(ifgf_options* opt);
  * Errors: IFGF_ERR_INVALID_ARG for N out of range, a non-finite coordinate, kappa < 0 or
  * non-finite, unsupported orders, levels outside {0} U [3, 21], all points coincident, or
  * two points sharing all three coordinates (G is singular there); IFGF_ERR_UNSUPPORTED when
- * a level's dense cone table would exceed the build's limit; IFGF_ERR_OOM, IFGF_ERR_CUDA.
+ * cone_table = 1 and a level's dense cone table would exceed 2^31 entries; IFGF_ERR_OOM
+ * (including a coefficient buffer of one density that does not fit), IFGF_ERR_CUDA.
  */
 ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, const int32_t* orders,
                              int32_t levels, const ifgf_options* opt, void* stream, ifgf_plan* out_plan);
@@ -130,14 +132,17 @@ ifgf_status ifgf_apply(ifgf_plan plan, const void* densities, int32_t nrhs, void
 ifgf_status ifgf_apply_ex(ifgf_plan plan, const void* densities, int32_t nrhs, void* out, void* stream,
                           int32_t near, int64_t level_mask);
 
-/* Release the plan and all its device memory (synchronous).  NULL is accepted. */
+/* Release the plan and all its device memory to the library's pool (synchronous; see
+ * ifgf_release_cached_memory).  NULL is accepted. */
 ifgf_status ifgf_plan_destroy(ifgf_plan plan);
 
 /*
  * Batched evaluation of many independent problems (each its own plan, e.g. bodies of different
- * sizes) as one launch sequence: the operator of Eq. (1) is applied to every plan in order.
- * The first ifgf_batch_apply with a given set of buffers captures the applies into a CUDA graph
- * on a private stream; later calls with the same buffers replay that graph with one launch on
+ * sizes) as one launch sequence: the operator of Eq. (1) is applied to every plan.  The first
+ * ifgf_batch_apply with a given set of buffers captures the applies into a CUDA graph on private
+ * streams (plan i on branch i mod 8 of a fork/join, so that independent problems run
+ * concurrently; each result is the same as the plan's own apply); later calls with the same
+ * buffers replay that graph with one launch on
  * `stream` (other buffers trigger a new capture).  Plans must live on one device, must outlive
  * the batch, and must not be applied elsewhere while the batch runs (they own their scratch).
  *
