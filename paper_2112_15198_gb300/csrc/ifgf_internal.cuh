@@ -626,12 +626,11 @@ __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0,
 //   B (8x8):   b0 (t, g), b1 (t+4, g)
 //   C (16x8):  c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
 // x = hi + lo for 3xTF32 products: hi keeps the sign, exponent and 10 leading mantissa bits of
-// x rounded to nearest (ties away from zero: add half an ulp of the 10-bit mantissa to the
-// magnitude bits, then clear the 13 low bits), so |lo| <= 2^-11 |x| and lo = x - hi is exact in
-// FP32. The tensor core reads the 10 leading mantissa bits of lo, which leaves a relative
-// error below 2^-21 |x| in hi + lo.
+// x (the 13 low bits cleared), so |lo| < 2^-10 |x| and lo = x - hi is exact in FP32. The tensor
+// core reads the 10 leading mantissa bits of lo, which leaves a relative error below 2^-20 |x|
+// in hi + lo; with the dropped lo*lo term a product keeps about 19 bits.
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
-    hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+    hi = __float_as_uint(x) & 0xffffe000u;
     lo = __float_as_uint(x - __uint_as_float(hi));
 }
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
