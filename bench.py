@@ -16,6 +16,7 @@ host cores, on a bounded sample of the same workload's targets.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -64,6 +65,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--nrhs", type=int, default=0,
+                    help="densities per apply (0: the workload's own count); for profiling cases")
     return ap.parse_args()
 
 
@@ -173,7 +176,7 @@ def run_reference(args, ws, rank):
     import oracle
 
     oracle.build()
-    w = W.make(args.workload)
+    w = workload_of(args)
     pts = w.points()
     dens = w.densities()
     threads = oracle.max_threads()
@@ -203,8 +206,15 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+def workload_of(args):
+    w = W.make(args.workload)
+    return dataclasses.replace(w, nrhs=args.nrhs) if args.nrhs > 0 else w
+
+
 def config_of(w, precision, D):
-    return {"workload": f"{w.name}: Fibonacci sphere, unit diameter, {w.wavelengths:g} wavelengths "
+    body = ("Fibonacci sphere, unit diameter" if w.geometry == "sphere"
+            else f"spheroid with semi-axes ({w.axes[0]:g}, {w.axes[0]:g}, {w.axes[1]:g})")
+    return {"workload": f"{w.name}: {body}, {w.wavelengths:g} wavelengths "
                         f"(kappa = 2 pi x {w.wavelengths:g}), N = {w.n}, nrhs = {w.nrhs}, densities iid U[-1,1]+iU[-1,1]",
             "N": w.n, "kappa": w.kappa, "nrhs": w.nrhs, "orders": [3, 5, 5], "precision": precision,
             "base_cones": [2, 4, 8], "tau": 0.5, "leaf_target": 64, "levels": D,
@@ -231,7 +241,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
     ifgf.load()
-    w = W.make(args.workload)
+    w = workload_of(args)
     pts = w.points()
     cdt = torch.complex64 if args.precision == "mixed" else torch.complex128
     dens_np = w.densities()
@@ -332,14 +342,27 @@ def main():
     kinds = {k: v for k, v in kt.items() if k in flops and v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
-    per_launch_flops = flops[dom] * args.steps / dom_n
+    # the work counts are per density; every density repeats the arithmetic
+    per_launch_flops = flops[dom] * w.nrhs * args.steps / dom_n
     achieved = per_launch_flops / (dom_ms / dom_n / 1e3) / 1e12
-    kernel_name = {"prop": "k_prop_warp_f32" if args.precision == "mixed" else "k_prop_f64",
-                   "interp": "k_interp_f32", "leaf": "k_leaf_box_f32", "near": "k_near_tile_f32"}[dom]
+    multi = w.nrhs > 1 and args.precision == "mixed"
+    kernel_name = {"prop": ("k_prop_mma_tab" if multi else "k_prop_warp_f32") if args.precision == "mixed"
+                   else "k_prop_f64",
+                   "interp": "k_interp_f32" if args.precision == "mixed" else "k_interp_f64",
+                   "leaf": ("k_leaf_f32_multi" if multi else "k_leaf_box_f32") if args.precision == "mixed"
+                   else "k_leaf_f64",
+                   "near": ("k_near_f32_multi" if multi else "k_near_tile_f32") if args.precision == "mixed"
+                   else "k_near_f64"}[dom]
+    bound = "alu"
     # FP32 (FP64) FMA throughput measured on this device by the probe kernels
     try:
         peaks = ifgf.measure_peaks()
-        if args.precision == "mixed":
+        if multi and dom == "prop":
+            # many-density propagation runs on the TF32 tensor cores (three products per product)
+            bound = "tensor"
+            peak = peaks["tf32_mma_sync_tflops"] / 3.0
+            peak_source = "measured: TF32 mma.sync probe on this GPU / 3 (3xTF32) (of measured)"
+        elif args.precision == "mixed":
             peak = max(peaks["fp32_ffma_tflops"], peaks["fp32x2_ffma2_tflops"])
             peak_source = "measured: FP32 FFMA/FFMA2 probe on this GPU (of measured)"
         else:
@@ -348,7 +371,7 @@ def main():
     except Exception as exc:  # the probe library is optional for the line itself
         peaks, peak = {"error": str(exc)}, PEAK_FP32_TFLOPS
         peak_source = "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (derived, not measured)"
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_record(kernel_name), "kernel": kernel_name,
                 "peak_source": peak_source, "peaks_measured": peaks,
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},

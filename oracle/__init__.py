@@ -9,6 +9,9 @@ O1  ``direct_sum``: the operator of Eq. (1) evaluated pair by pair in FP64.
 O2  ``Plan``: the plain CPU IFGF (tree, cousins, relevant cones of Eq. (4),
     Algorithms 5-8) in FP64, with its integer lists exposed for bit-exact
     comparison.
+S1  ``stokes_direct_sum``: Eq. (1) with the Stokeslet (Stokes Green tensor at
+    unit viscosity) acting on real force vectors, pair by pair in FP64.
+S2  ``Plan.apply_stokes``: the O2 IFGF for the Stokeslet on a kappa = 0 plan.
 
 Parity unpinned: none of the functions here lacks a pin; see ``tests/test_oracle_*``.
 """
@@ -70,6 +73,10 @@ def _load():
         lib.orc_plan_destroy.restype = None
         lib.orc_apply.argtypes = [c_vp, c_int, c_vp, c_vp, c_int, c_i64]
         lib.orc_apply.restype = c_int
+        lib.orc_stokes_direct_sum.argtypes = [c_i64, c_vp, c_vp, c_vp, c_int, c_vp, c_i64, c_vp, c_vp]
+        lib.orc_stokes_direct_sum.restype = None
+        lib.orc_apply_stokes.argtypes = [c_vp, c_int, c_vp, c_vp, c_int, c_i64]
+        lib.orc_apply_stokes.restype = c_int
         lib.orc_get.argtypes = [c_vp, c_int, c_int, c_vp]
         lib.orc_get.restype = c_i64
         lib.orc_info.argtypes = [c_vp, c_vp, c_vp]
@@ -113,6 +120,24 @@ def direct_sum(points: np.ndarray, kappa: float, dens: np.ndarray, tgt=None) -> 
     out = np.zeros((nrhs, t.shape[0]), dtype=np.complex128)
     x, y, z = (np.ascontiguousarray(pts[i]) for i in range(3))
     lib.orc_direct_sum(n, _ptr(x), _ptr(y), _ptr(z), float(kappa), nrhs, _ptr(a), t.shape[0], _ptr(t), _ptr(out))
+    return out
+
+
+def stokes_direct_sum(points: np.ndarray, forces: np.ndarray, tgt=None) -> np.ndarray:
+    """S1: u_i(x_l) = sum_{m != l} sum_j S_ij(x_l, x_m) f_j(x_m), S the Stokeslet at unit
+    viscosity, S_ij = (delta_ij/r + r_i r_j/r^3)/(8 pi), at target indices tgt.
+
+    points (3, N) float64; forces (nf, 3, N) or (3, N) real; returns (nf, 3, M) float64.
+    """
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n = pts.shape[1]
+    f = np.ascontiguousarray(np.asarray(forces, dtype=np.float64).reshape(-1, 3, n))
+    nf = f.shape[0]
+    t = np.arange(n, dtype=np.int64) if tgt is None else np.ascontiguousarray(tgt, dtype=np.int64)
+    out = np.zeros((nf, 3, t.shape[0]), dtype=np.float64)
+    x, y, z = (np.ascontiguousarray(pts[i]) for i in range(3))
+    lib.orc_stokes_direct_sum(n, _ptr(x), _ptr(y), _ptr(z), nf, _ptr(f), t.shape[0], _ptr(t), _ptr(out))
     return out
 
 
@@ -208,6 +233,16 @@ class Plan:
         st = self._lib.orc_apply(self._h, a.shape[0], _ptr(a), _ptr(out), 1 if near else 0, int(level_mask))
         if st != 0:
             raise OracleError(f"orc_apply failed with status {st}")
+        return out
+
+    def apply_stokes(self, forces: np.ndarray, near: bool = True, level_mask: int = -1) -> np.ndarray:
+        """FP64 IFGF apply of the Stokeslet (kappa = 0 plans); forces (nf, 3, N) or (3, N) real in the
+        caller's order -> velocities (nf, 3, N)."""
+        f = np.ascontiguousarray(np.asarray(forces, dtype=np.float64).reshape(-1, 3, self.N))
+        out = np.zeros_like(f)
+        st = self._lib.orc_apply_stokes(self._h, f.shape[0], _ptr(f), _ptr(out), 1 if near else 0, int(level_mask))
+        if st != 0:
+            raise OracleError(f"orc_apply_stokes failed with status {st}")
         return out
 
     def work(self) -> dict:

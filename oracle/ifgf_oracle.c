@@ -15,6 +15,9 @@
  *                           LevelDEvaluations (Algorithm 6), then for d = D..3
  *                           Interpolation(d) (Algorithm 8) and Propagation(d)
  *                           (Algorithm 7), as ordered by Algorithm 5.
+ *   S1  orc_stokes_direct_sum   Eq. (1) with the Stokes Green tensor (the Stokeslet),
+ *                           one of the kernels Sec. 2 names, FP64, compensated sums.
+ *   S2  orc_apply_stokes    the same IFGF steps for the Stokeslet on a kappa = 0 plan.
  *
  * The paper defers the numerical details of IFGF (analytic factor, the
  * singularity-resolving radial variable, interpolation nodes, cone counts) to
@@ -37,7 +40,13 @@
  *   - the relevant-cone test of Eq. (4) is taken in its discrete form: a cone is
  *     relevant iff a cousin point or a node of a relevant parent cone lies in it;
  *   - the point order is the sort by the 60-bit level-21 Morton key, ties broken
- *     by the original index (the paper leaves the order inside a box arbitrary).
+ *     by the original index (the paper leaves the order inside a box arbitrary);
+ *   - Stokes kernel: the Stokeslet at unit viscosity,
+ *     S_ij(x,y) = (delta_ij/r + (x_i-y_i)(x_j-y_j)/r^3)/(8 pi), acting on real force
+ *     vectors f_m; its centred factor is the Laplace one, G_0(x,x_k) = 1/(4 pi |x-x_k|),
+ *     and its analytic factor S_ij(x,x')/G_0(x,x_k) (Eq. (3) with a matrix-valued G),
+ *     so that propagation and interpolation are those of the kappa = 0 kernel applied
+ *     to each of the three velocity components.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared  (no -ffast-math:
  * classification relies on IEEE single precision without contraction).
@@ -104,6 +113,42 @@ void orc_direct_sum(int64_t N, const double* x, const double* y, const double* z
         }
         for (int q = 0; q < nrhs; ++q)
             out[(int64_t)q * M + t] = (acc[2 * q].s + acc[2 * q].c) + I * (acc[2 * q + 1].s + acc[2 * q + 1].c);
+        free(acc);
+    }
+}
+
+/* Stokeslet at unit viscosity for the separation v = x - y (a reading; Sec. 2 names the
+ * Stokes equations among the kernels of Eq. (1)):
+ * S_ij = (delta_ij / r + v_i v_j / r^3) / (8 pi). */
+static void stokeslet(const double* v, double S[3][3]) {
+    const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S[i][j] = ((i == j ? 1.0 / r : 0.0) + v[i] * v[j] / (r * r * r)) / (8.0 * M_PI);
+}
+
+/*
+ * S1: u_i(x_l) = sum_{m != l} sum_j S_ij(x_l, x_m) f_j(x_m)  (Eq. (1) with the Stokeslet),
+ * at the M target indices tgt[], for every force field s < nf.  f is [nf][3][N] real,
+ * out is [nf][3][M].
+ */
+void orc_stokes_direct_sum(int64_t N, const double* x, const double* y, const double* z, int nf,
+                           const double* f, int64_t M, const int64_t* tgt, double* out) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < M; ++t) {
+        const int64_t l = tgt[t];
+        ksum* acc = (ksum*)calloc((size_t)3 * nf, sizeof(ksum));
+        for (int64_t m = 0; m < N; ++m) {
+            if (m == l) continue;
+            const double v[3] = {x[l] - x[m], y[l] - y[m], z[l] - z[m]};
+            double S[3][3];
+            stokeslet(v, S);
+            for (int q = 0; q < nf; ++q)
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        ksum_add(&acc[3 * q + i], S[i][j] * f[((int64_t)3 * q + j) * N + m]);
+        }
+        for (int c = 0; c < 3 * nf; ++c) out[(int64_t)c * M + t] = acc[c].s + acc[c].c;
         free(acc);
     }
 }
@@ -741,7 +786,15 @@ int orc_has_duplicates(const orc_plan* p) {
  * near != 0 adds the level-D neighbour interactions; bit d of level_mask adds the
  * level-d cousin interpolations (all levels: ~0).
  */
-int orc_apply(orc_plan* p, int nrhs, const cplx* a, cplx* out, int near, int64_t level_mask) {
+/*
+ * The IFGF apply on nrhs channels.  Helmholtz (stokes = 0): channel q is density vector q.
+ * Stokes (stokes = 1, kappa = 0): channel 3s+j holds component j of force field s (real
+ * values in complex storage); the near field and the leaf evaluation contract the
+ * Stokeslet with the force vector, everything after the leaf level acts on each channel
+ * alone, as it does for the kappa = 0 kernel.
+ */
+static int apply_impl(orc_plan* p, int stokes, int nrhs, const cplx* a, cplx* out, int near,
+                      int64_t level_mask) {
     const int64_t N = p->N;
     const int D = p->D, P = p->P, Ps = p->Ps, Pt = p->Pt, Pp = p->Pp;
     const double kappa = p->kappa;
@@ -764,8 +817,18 @@ int orc_apply(orc_plan* p, int nrhs, const cplx* a, cplx* out, int near, int64_t
                         if (j == i) continue;
                         double dx = p->X[0][i] - p->X[0][j], dy = p->X[1][i] - p->X[1][j],
                                dz = p->X[2][i] - p->X[2][j];
-                        cplx g = green(kappa, sqrt(dx * dx + dy * dy + dz * dz));
                         ++wnear;
+                        if (stokes) {
+                            const double v[3] = {dx, dy, dz};
+                            double S[3][3];
+                            stokeslet(v, S);
+                            for (int q = 0; q < nrhs / 3; ++q)
+                                for (int c = 0; c < 3; ++c)
+                                    for (int e = 0; e < 3; ++e)
+                                        I_[(int64_t)(3 * q + c) * N + i] += S[c][e] * as[(int64_t)(3 * q + e) * N + j];
+                            continue;
+                        }
+                        cplx g = green(kappa, sqrt(dx * dx + dy * dy + dz * dz));
                         for (int r = 0; r < nrhs; ++r) I_[(int64_t)r * N + i] += as[(int64_t)r * N + j] * g;
                     }
                 }
@@ -793,9 +856,21 @@ int orc_apply(orc_plan* p, int nrhs, const cplx* a, cplx* out, int near, int64_t
                                     (yv[2] - xc[2]) * (yv[2] - xc[2]));
                     for (int64_t j = LD->start[b]; j < LD->start[b + 1]; ++j) {
                         double dx = yv[0] - p->X[0][j], dy = yv[1] - p->X[1][j], dz = yv[2] - p->X[2][j];
+                        ++wleaf;
+                        if (stokes) {
+                            /* analytic factor S_ij(y, x') / G_0(y, x_k), G_0(y, x_k) = 1/(4 pi r) */
+                            const double v[3] = {dx, dy, dz};
+                            double S[3][3];
+                            stokeslet(v, S);
+                            for (int q = 0; q < nrhs / 3; ++q)
+                                for (int c = 0; c < 3; ++c)
+                                    for (int e = 0; e < 3; ++e)
+                                        f[(int64_t)(3 * q + c) * P + n] +=
+                                            (4.0 * M_PI * r) * S[c][e] * as[(int64_t)(3 * q + e) * N + j];
+                            continue;
+                        }
                         double dist = sqrt(dx * dx + dy * dy + dz * dz);
                         cplx g = (r / dist) * cexp(I * kappa * (dist - r));
-                        ++wleaf;
                         for (int q = 0; q < nrhs; ++q) f[(int64_t)q * P + n] += as[(int64_t)q * N + j] * g;
                     }
                 }
@@ -893,6 +968,25 @@ int orc_apply(orc_plan* p, int nrhs, const cplx* a, cplx* out, int near, int64_t
     free(as);
     free(I_);
     return bad ? ORC_ERR_INTERNAL : ORC_OK;
+}
+
+int orc_apply(orc_plan* p, int nrhs, const cplx* a, cplx* out, int near, int64_t level_mask) {
+    return apply_impl(p, 0, nrhs, a, out, near, level_mask);
+}
+
+/* S2: u = IFGF approximation of S1 at every point; f and u are [nf][3][N] real in the
+ * caller's point order.  The plan must have kappa = 0. */
+int orc_apply_stokes(orc_plan* p, int nf, const double* f, double* u, int near, int64_t level_mask) {
+    if (p->kappa != 0.0 || nf < 1) return ORC_ERR_ARG;
+    const int64_t n = (int64_t)3 * nf * p->N;
+    cplx* a = (cplx*)xcalloc((size_t)n, sizeof(cplx));
+    cplx* o = (cplx*)xcalloc((size_t)n, sizeof(cplx));
+    for (int64_t i = 0; i < n; ++i) a[i] = f[i];
+    int st = apply_impl(p, 1, 3 * nf, a, o, near, level_mask);
+    for (int64_t i = 0; i < n; ++i) u[i] = creal(o[i]);
+    free(a);
+    free(o);
+    return st;
 }
 
 /* ------------------------------------------------------------------------- */
