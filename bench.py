@@ -39,17 +39,24 @@ UNIT = "pts/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # Algorithmic FP32 flops per unit of work (counted from the arithmetic of the method's
-# steps, independent of how the kernels schedule it):
-#   interpolant evaluation at one point, orders (3,5,5): separable contraction
-#   4*(75+15+3) = 372, Chebyshev recurrences 2*(1+3+3) = 14, local coordinates 6,
-#   squared distance 5, factor/ratio multiply-accumulate 18  -> 415
-FLOPS_INTERP_EVAL = 415
-#   coefficient generation per node: 4*(5+5+3) = 52
+# steps, independent of how the kernels schedule it), split into the part shared by all value
+# sets of an apply and the part repeated for each (complex) set:
+#   interpolant evaluation at one point, orders (3,5,5): Chebyshev recurrences 2*(1+3+3) = 14,
+#   local coordinates 6, squared distance 5 (shared: 25); per set the separable contraction
+#   4*(75+15+3) = 372 and the factor/ratio multiply-accumulate 18 (390)  -> 415 for one set
+FLOPS_EVAL_SHARED, FLOPS_EVAL_SET = 25, 390
+#   centred factor of an interpolation to a target (shared): 10
+FLOPS_CENTRED = 10
+#   coefficient generation per node and set: 4*(5+5+3) = 52
 FLOPS_DCT_NODE = 52
-#   leaf pair (analytic factor of one source at one node, accumulate): 35
-FLOPS_LEAF_PAIR = 35
-#   near-field pair (distance, Green function, accumulate): 22
-FLOPS_NEAR_PAIR = 22
+#   Helmholtz leaf pair: analytic factor of one source at one node 27, accumulate 8 per set
+FLOPS_LEAF_SHARED, FLOPS_LEAF_SET = 27, 8
+#   Helmholtz near-field pair: distance and Green function 14, accumulate 8 per set
+FLOPS_NEAR_SHARED, FLOPS_NEAR_SET = 14, 8
+#   Stokeslet pairs (per force field: r.f 5, scaling 1, three two-FMA accumulations 12):
+#   near field separation 3 + squared distance 5 + 1/r^2 1; leaf w 9 + |w|^2 5 + 1/|w|^2 1
+FLOPS_STOKES_FIELD = 18
+FLOPS_STOKES_NEAR_SHARED, FLOPS_STOKES_LEAF_SHARED = 9, 15
 # FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.070 GHz (maximum SM clock).
 SMS, LANES, MAX_SM_GHZ = 152, 128, 2.070
 PEAK_FP32_TFLOPS = SMS * LANES * 2 * MAX_SM_GHZ / 1e3
@@ -66,7 +73,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--nrhs", type=int, default=0,
-                    help="densities per apply (0: the workload's own count); for profiling cases")
+                    help="densities (force fields for --kernel stokes) per apply; 0: the workload's own count")
+    ap.add_argument("--kernel", default="helmholtz", choices=["helmholtz", "stokes"],
+                    help="stokes: the Stokeslet on the workload's points (kappa = 0, real force fields)")
     return ap.parse_args()
 
 
@@ -129,13 +138,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_flops(work: dict, ncone: dict, P: int) -> dict:
-    prop = sum(work["prop"].values()) * FLOPS_INTERP_EVAL
-    prop += sum(ncone[d] for d in ncone if d < max(ncone)) * P * FLOPS_DCT_NODE
-    interp = sum(work["interp"].values()) * (FLOPS_INTERP_EVAL + 10)
-    leaf = work["leaf_pairs"] * FLOPS_LEAF_PAIR + ncone[max(ncone)] * P * FLOPS_DCT_NODE
-    near = work["near_pairs"] * FLOPS_NEAR_PAIR
+def algorithmic_flops(work: dict, ncone: dict, P: int, sets: int, stokes_fields: int = 0) -> dict:
+    """FP32 flops of one apply on `sets` complex value sets (for the Stokeslet, its
+    ceil(3 nf / 2) sets of nf force fields)."""
+    top = max(ncone)
+    prop = sum(work["prop"].values()) * (FLOPS_EVAL_SHARED + FLOPS_EVAL_SET * sets)
+    prop += sum(ncone[d] for d in ncone if d < top) * P * FLOPS_DCT_NODE * sets
+    interp = sum(work["interp"].values()) * (FLOPS_EVAL_SHARED + FLOPS_CENTRED + FLOPS_EVAL_SET * sets)
+    dct_leaf = ncone[top] * P * FLOPS_DCT_NODE * sets
+    if stokes_fields:
+        leaf = work["leaf_pairs"] * (FLOPS_STOKES_LEAF_SHARED + FLOPS_STOKES_FIELD * stokes_fields) + dct_leaf
+        near = work["near_pairs"] * (FLOPS_STOKES_NEAR_SHARED + FLOPS_STOKES_FIELD * stokes_fields)
+    else:
+        leaf = work["leaf_pairs"] * (FLOPS_LEAF_SHARED + FLOPS_LEAF_SET * sets) + dct_leaf
+        near = work["near_pairs"] * (FLOPS_NEAR_SHARED + FLOPS_NEAR_SET * sets)
     return {"prop": prop, "interp": interp, "leaf": leaf, "near": near}
+
+
+def kernel_source_sha(kernel: str, apply_src: str, header_src: str) -> str:
+    """sha256 prefix of a kernel's definition in apply.cu together with the device helpers of
+    ifgf_internal.cuh (everything after its "Device helpers" banner)."""
+    at = apply_src.index(f"\n{kernel}(")
+    start = apply_src.rindex("\n\n", 0, at)
+    end = apply_src.index("\n}\n", at) + 3
+    dev = header_src[header_src.index("// Device helpers"):]
+    return hashlib.sha256((apply_src[start:end] + dev).encode()).hexdigest()[:16]
 
 
 def traffic_record(kernel: str):
@@ -144,11 +171,15 @@ def traffic_record(kernel: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    src = open(os.path.join(ROOT, "paper_2112_15198_gb300", "csrc", "apply.cu"), "rb").read()
-    sha = hashlib.sha256(src).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2112_15198_gb300", "csrc")
+    try:
+        sha = kernel_source_sha(kernel, open(os.path.join(csrc, "apply.cu")).read(),
+                                open(os.path.join(csrc, "ifgf_internal.cuh")).read())
+    except ValueError:
+        return None
     for ln in open(path):
         f = dict(kv.split("=", 1) for kv in ln.split() if "=" in kv)
-        if f.get("kernel") == kernel and f.get("apply_sha") == sha and "bytes_per_launch" in f:
+        if f.get("kernel") == kernel and f.get("source_sha") == sha and "bytes_per_launch" in f:
             return float(f["bytes_per_launch"])
     return None
 
@@ -177,30 +208,32 @@ def run_reference(args, ws, rank):
 
     oracle.build()
     w = workload_of(args)
+    prob = Problem(args, w)
     pts = w.points()
-    dens = w.densities()
+    dens = prob.host_inputs()
     threads = oracle.max_threads()
     # bounded sample: enough targets for ~3 s of CPU work per step
     probe = W.targets(w.n, 64, 999)
-    oracle.direct_sum(pts, w.kappa, dens, probe[:4])  # thread pool start-up, untimed
+    prob.exact(oracle, pts, dens, probe[:4])  # thread pool start-up, untimed
     t0 = time.perf_counter()
-    oracle.direct_sum(pts, w.kappa, dens, probe)
+    prob.exact(oracle, pts, dens, probe)
     per_target = (time.perf_counter() - t0) / len(probe)
     m = int(max(16, min(w.n, 3.0 / per_target)))
     tg = W.targets(w.n, m, w.seed + 200)
     for _ in range(args.warmup):
-        oracle.direct_sum(pts, w.kappa, dens, tg[:16])
+        prob.exact(oracle, pts, dens, tg[:16])
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.direct_sum(pts, w.kappa, dens, tg)
+        prob.exact(oracle, pts, dens, tg)
         times.append(time.perf_counter() - t0)
     value = m * w.nrhs / statistics.median(times)
-    sample = f"direct sum of Eq. (1) at {m} of the {w.n} targets per step (FP64, OpenMP)"
+    what = "the Stokeslet sum" if prob.stokes else "Eq. (1)"
+    sample = f"direct sum of {what} at {m} of the {w.n} targets per step (FP64, OpenMP)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config_of(w, args.precision, None),
+           "config": config_of(w, args.precision, None, prob.stokes),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -208,14 +241,60 @@ def run_reference(args, ws, rank):
 
 def workload_of(args):
     w = W.make(args.workload)
-    return dataclasses.replace(w, nrhs=args.nrhs) if args.nrhs > 0 else w
+    if args.nrhs > 0:
+        w = dataclasses.replace(w, nrhs=args.nrhs)
+    if args.kernel == "stokes":
+        w = dataclasses.replace(w, wavelengths=0.0)
+    return w
 
 
-def config_of(w, precision, D):
+class Problem:
+    """The apply of one kernel on a workload: inputs, plan and oracle reference."""
+
+    def __init__(self, args, w):
+        self.w, self.stokes, self.precision = w, args.kernel == "stokes", args.precision
+        # complex value sets carried through the levels
+        self.sets = (3 * w.nrhs + 1) // 2 if self.stokes else w.nrhs
+
+    def host_inputs(self):
+        if self.stokes:
+            rng = np.random.default_rng(self.w.seed + 100)
+            return rng.uniform(-1.0, 1.0, (self.w.nrhs, 3, self.w.n))
+        return self.w.densities()
+
+    def torch_inputs(self, host):
+        import torch
+
+        if self.stokes:
+            return torch.from_numpy(host.astype(np.float32))
+        cdt = torch.complex64 if self.precision == "mixed" else torch.complex128
+        return torch.from_numpy(host).to(cdt)
+
+    def plan(self, ifgf, P):
+        return ifgf.Plan(P, self.w.kappa, precision=self.precision, max_nrhs=self.sets)
+
+    def apply(self, plan, A, out):
+        if self.stokes:
+            plan.apply_stokes(A, out)
+        else:
+            plan.apply(A, out)
+
+    def exact(self, oracle, pts, host, tgt):
+        if self.stokes:
+            return oracle.stokes_direct_sum(pts, host, tgt)
+        return oracle.direct_sum(pts, self.w.kappa, host, tgt)
+
+
+def config_of(w, precision, D, stokes=False):
     body = ("Fibonacci sphere, unit diameter" if w.geometry == "sphere"
             else f"spheroid with semi-axes ({w.axes[0]:g}, {w.axes[0]:g}, {w.axes[1]:g})")
-    return {"workload": f"{w.name}: {body}, {w.wavelengths:g} wavelengths "
-                        f"(kappa = 2 pi x {w.wavelengths:g}), N = {w.n}, nrhs = {w.nrhs}, densities iid U[-1,1]+iU[-1,1]",
+    if stokes:
+        what = (f"{w.name} points: {body}, Stokeslet (unit viscosity), N = {w.n}, nrhs = {w.nrhs} force fields "
+                f"iid U[-1,1]^3")
+    else:
+        what = (f"{w.name}: {body}, {w.wavelengths:g} wavelengths (kappa = 2 pi x {w.wavelengths:g}), N = {w.n}, "
+                f"nrhs = {w.nrhs}, densities iid U[-1,1]+iU[-1,1]")
+    return {"workload": what,
             "N": w.n, "kappa": w.kappa, "nrhs": w.nrhs, "orders": [3, 5, 5], "precision": precision,
             "base_cones": [2, 4, 8], "tau": 0.5, "leaf_target": 64, "levels": D,
             "step": "ifgf_plan_create + ifgf_apply + ifgf_plan_destroy (device-resident inputs)",
@@ -242,11 +321,11 @@ def main():
         pg = dist
     ifgf.load()
     w = workload_of(args)
+    prob = Problem(args, w)
     pts = w.points()
-    cdt = torch.complex64 if args.precision == "mixed" else torch.complex128
-    dens_np = w.densities()
+    dens_np = prob.host_inputs()
     P_host = torch.from_numpy(pts).pin_memory()
-    A_host = torch.from_numpy(dens_np).to(cdt).pin_memory()
+    A_host = prob.torch_inputs(dens_np).pin_memory()
     P = P_host.to(dev)
     A = A_host.to(dev)
     out = torch.empty_like(A)
@@ -254,8 +333,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        plan = ifgf.Plan(P, w.kappa, precision=args.precision, max_nrhs=w.nrhs)
-        plan.apply(A, out)
+        plan = prob.plan(ifgf, P)
+        prob.apply(plan, A, out)
         plan.destroy()
 
     for _ in range(args.warmup):
@@ -291,16 +370,16 @@ def main():
     value = whole_job_value(ws, w.n, w.nrhs, ms_step)
 
     # ---- apply-only throughput on a persistent plan (context) ------------------------
-    plan = ifgf.Plan(P, w.kappa, precision=args.precision, max_nrhs=w.nrhs)
+    plan = prob.plan(ifgf, P)
     for _ in range(2):
-        plan.apply(A, out)
+        prob.apply(plan, A, out)
     torch.cuda.synchronize()
     ap_ms = []
     for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan.apply(A, out)
+        prob.apply(plan, A, out)
         e1.record(stream)
         e1.synchronize()
         ap_ms.append(e0.elapsed_time(e1))
@@ -310,7 +389,7 @@ def main():
     status = plan.status()
 
     # ---- end to end through the C ABI with host buffers ------------------------------
-    out_host = torch.empty(A.shape, dtype=cdt).pin_memory()
+    out_host = torch.empty(A.shape, dtype=A.dtype).pin_memory()
     Pd = torch.empty_like(P)
     Ad = torch.empty_like(A)
     e2e_ms = []
@@ -320,8 +399,8 @@ def main():
         t0 = time.perf_counter()
         Pd.copy_(P_host, non_blocking=True)
         Ad.copy_(A_host, non_blocking=True)
-        pl = ifgf.Plan(Pd, w.kappa, precision=args.precision, max_nrhs=w.nrhs)
-        pl.apply(Ad, out)
+        pl = prob.plan(ifgf, Pd)
+        prob.apply(pl, Ad, out)
         out_host.copy_(out, non_blocking=True)
         torch.cuda.synchronize()
         pl.destroy()
@@ -338,21 +417,22 @@ def main():
         return
 
     # ---- roofline of the dominant kernel ----------------------------------------------
-    flops = algorithmic_flops(work, ncone, 75)
+    flops = algorithmic_flops(work, ncone, 75, prob.sets, w.nrhs if prob.stokes else 0)
     kinds = {k: v for k, v in kt.items() if k in flops and v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
-    # the work counts are per density; every density repeats the arithmetic
-    per_launch_flops = flops[dom] * w.nrhs * args.steps / dom_n
+    per_launch_flops = flops[dom] * args.steps / dom_n
     achieved = per_launch_flops / (dom_ms / dom_n / 1e3) / 1e12
-    multi = w.nrhs > 1 and args.precision == "mixed"
-    kernel_name = {"prop": ("k_prop_mma_tab" if multi else "k_prop_warp_f32") if args.precision == "mixed"
-                   else "k_prop_f64",
-                   "interp": "k_interp_f32" if args.precision == "mixed" else "k_interp_f64",
-                   "leaf": ("k_leaf_f32_multi" if multi else "k_leaf_box_f32") if args.precision == "mixed"
-                   else "k_leaf_f64",
-                   "near": ("k_near_f32_multi" if multi else "k_near_tile_f32") if args.precision == "mixed"
-                   else "k_near_f64"}[dom]
+    multi = prob.sets >= 4 and args.precision == "mixed"  # the tensor-core path
+    if args.precision != "mixed":
+        kernel_name = {"prop": "k_prop_f64", "interp": "k_interp_f64", "leaf": "k_leaf_f64", "near": "k_near_f64"}[dom]
+    elif prob.stokes:
+        kernel_name = {"prop": "k_prop_mma_tab" if multi else "k_prop_warp_f32", "interp": "k_interp_f32",
+                       "leaf": "k_leaf_stokes_f32", "near": "k_near_stokes_f32"}[dom]
+    else:
+        kernel_name = {"prop": "k_prop_mma_tab" if multi else "k_prop_warp_f32", "interp": "k_interp_f32",
+                       "leaf": "k_leaf_f32_multi" if multi else "k_leaf_box_f32",
+                       "near": "k_near_f32_multi" if multi else "k_near_tile_f32"}[dom]
     bound = "alu"
     # FP32 (FP64) FMA throughput measured on this device by the probe kernels
     try:
@@ -380,7 +460,7 @@ def main():
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-           "config": config_of(w, args.precision, D),
+           "config": config_of(w, args.precision, D, prob.stokes),
            "e2e": {"value": whole_job_value(ws, w.n, w.nrhs, e2e_step), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
@@ -397,18 +477,19 @@ def main():
         oracle.build()
         threads = oracle.max_threads()
         probe = W.targets(w.n, 64, 999)
-        oracle.direct_sum(pts, w.kappa, dens_np, probe[:4])  # thread pool start-up, untimed
+        prob.exact(oracle, pts, dens_np, probe[:4])  # thread pool start-up, untimed
         t0 = time.perf_counter()
-        oracle.direct_sum(pts, w.kappa, dens_np, probe)
+        prob.exact(oracle, pts, dens_np, probe)
         per_target = (time.perf_counter() - t0) / len(probe)
         m = int(max(16, min(w.n, args.cpu_seconds / per_target)))
         tg = W.targets(w.n, m, w.seed + 200)
         t0 = time.perf_counter()
-        exact = oracle.direct_sum(pts, w.kappa, dens_np, tg)
+        exact = prob.exact(oracle, pts, dens_np, tg)
         el = time.perf_counter() - t0
-        got = out.cpu().numpy().astype(np.complex128)[:, tg]
+        got = out.cpu().numpy().astype(np.complex128 if not prob.stokes else np.float64)[..., tg]
+        what = "the Stokeslet sum" if prob.stokes else "Eq. (1)"
         res["cpu_baseline"] = {"value": m * w.nrhs / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": f"FP64 direct sum of Eq. (1) at {m} of the {w.n} targets ({el:.1f} s)"}
+                               "sample": f"FP64 direct sum of {what} at {m} of the {w.n} targets ({el:.1f} s)"}
         res["rel_err_vs_direct_sum"] = {"value": oracle.rel_l2(got, exact), "targets": m}
     print(json.dumps(res), flush=True)
     if pg:

@@ -132,6 +132,32 @@ ifgf_status ifgf_apply(ifgf_plan plan, const void* densities, int32_t nrhs, void
 ifgf_status ifgf_apply_ex(ifgf_plan plan, const void* densities, int32_t nrhs, void* out, void* stream,
                           int32_t near, int64_t level_mask);
 
+/*
+ * Stokes kernel: velocities of point forces in Stokes flow at unit viscosity,
+ *     u_i(x_l) = sum_{m != l} sum_j S_ij(x_l, x_m) f_j(x_m),
+ *     S_ij(x, y) = (delta_ij / r + (x_i - y_i)(x_j - y_j) / r^3) / (8 pi),  r = |x - y|,
+ * i.e. Eq. (1) with the Green tensor of the Stokes equations (one of the kernels Sec. 2 names),
+ * evaluated by the same IFGF steps: the centred factor is the Laplace one, 1/(4 pi |x - x_k|),
+ * and the analytic factor of Eq. (3) is S(x, x') divided by it.  Asynchronous on `stream`, like
+ * ifgf_apply.
+ *
+ *   plan      created with kappa = 0 and precision IFGF_PREC_MIXED, and with
+ *             opt.max_nrhs >= ceil(3 nfield / 2) (the three velocity components of a field are
+ *             carried as real and imaginary parts of complex value sets, two per set).
+ *   forces    device, [nfield][3][N] float32 (component-major per field), the caller's point
+ *             order.  Read only.
+ *   nfield    number of force fields, >= 1.
+ *   velocity  device, same layout and type as forces; overwritten.  Must not alias it.
+ *
+ * Errors: IFGF_ERR_INVALID_ARG for NULL pointers, aliasing, kappa != 0 or nfield out of range;
+ * IFGF_ERR_UNSUPPORTED for an FP64 plan.
+ */
+ifgf_status ifgf_apply_stokes(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream);
+
+/* ifgf_apply_stokes restricted to some contributions, as ifgf_apply_ex. */
+ifgf_status ifgf_apply_stokes_ex(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream,
+                                 int32_t near, int64_t level_mask);
+
 /* Release the plan and all its device memory to the library's pool (synchronous; see
  * ifgf_release_cached_memory).  NULL is accepted. */
 ifgf_status ifgf_plan_destroy(ifgf_plan plan);

@@ -83,6 +83,10 @@ def load(build: bool = True):
         lib.ifgf_apply.restype = ctypes.c_int
         lib.ifgf_apply_ex.argtypes = [vp, vp, i32, vp, vp, i32, i64]
         lib.ifgf_apply_ex.restype = ctypes.c_int
+        lib.ifgf_apply_stokes.argtypes = [vp, vp, i32, vp, vp]
+        lib.ifgf_apply_stokes.restype = ctypes.c_int
+        lib.ifgf_apply_stokes_ex.argtypes = [vp, vp, i32, vp, vp, i32, i64]
+        lib.ifgf_apply_stokes_ex.restype = ctypes.c_int
         lib.ifgf_plan_destroy.argtypes = [vp]
         lib.ifgf_plan_destroy.restype = ctypes.c_int
         lib.ifgf_plan_query.argtypes = [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -219,6 +223,19 @@ class Plan:
             _check(self._lib.ifgf_apply_ex(self._h, _ptr(dens), int(nrhs), _ptr(out), _stream(stream),
                                            1 if near else 0, int(level_mask)))
         return out
+
+    def apply_stokes(self, forces, velocity, nfield: int | None = None, stream=None, near: bool = True,
+                     level_mask: int = -1):
+        """velocity <- Stokeslet sums of the force fields (kappa = 0 MIXED plans); forces/velocity are
+        [nfield][3][N] float32 in the caller's point order."""
+        if nfield is None:
+            nfield = 1 if len(forces.shape) == 2 else int(forces.shape[0])
+        if near and level_mask == -1:
+            _check(self._lib.ifgf_apply_stokes(self._h, _ptr(forces), int(nfield), _ptr(velocity), _stream(stream)))
+        else:
+            _check(self._lib.ifgf_apply_stokes_ex(self._h, _ptr(forces), int(nfield), _ptr(velocity), _stream(stream),
+                                                  1 if near else 0, int(level_mask)))
+        return velocity
 
     def query(self, what: int, level: int = 0) -> np.ndarray:
         cnt = ctypes.c_int64(0)

@@ -304,6 +304,39 @@ ifgf_status ifgf_apply(ifgf_plan plan, const void* densities, int32_t nrhs, void
     return ifgf_apply_ex(plan, densities, nrhs, out, stream, 1, -1);
 }
 
+ifgf_status ifgf_apply_stokes_ex(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream,
+                                 int32_t near, int64_t level_mask) {
+    if (!plan || !forces || !velocity) {
+        set_last_error("NULL plan, forces or velocity");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    if (forces == velocity) {
+        set_last_error("velocity must not alias forces");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    if (plan->kappa != 0.0) {
+        set_last_error("the Stokes kernel needs a plan created with kappa = 0");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    if (plan->precision != IFGF_PREC_MIXED) {
+        set_last_error("the Stokes kernel is built for IFGF_PREC_MIXED plans");
+        return IFGF_ERR_UNSUPPORTED;
+    }
+    if (nfield < 1 || (3 * (int64_t)nfield + 1) / 2 > plan->max_nrhs) {
+        set_last_error("nfield must be in [1, 2 max_nrhs / 3]");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    return guard([&] {
+        IFGF_CUDA(cudaSetDevice(plan->device));
+        apply_plan_stokes(*plan, static_cast<const float*>(forces), nfield, static_cast<float*>(velocity),
+                          (cudaStream_t)stream, near != 0, level_mask);
+    });
+}
+
+ifgf_status ifgf_apply_stokes(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream) {
+    return ifgf_apply_stokes_ex(plan, forces, nfield, velocity, stream, 1, -1);
+}
+
 ifgf_status ifgf_plan_destroy(ifgf_plan plan) {
     if (!plan) return IFGF_OK;
     ifgf_status st = guard([&] {

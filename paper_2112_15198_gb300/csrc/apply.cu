@@ -1207,6 +1207,62 @@ __global__ void k_near_f32_multi(int64_t N, const int32_t* __restrict__ pboxD, c
         if (rhs0 + r < nrhs) Is[(int64_t)(rhs0 + r) * N + i] = acc[r];
 }
 
+// Chebyshev coefficients of NR value sets f[r][.] of one cone (separable analysis by the
+// matrices Ws | Wt | Wp, last index first), stored to out[r * cstride + m] for r < nv; tmp is
+// scratch of the same size. Every thread of the block calls it (it synchronises the block).
+template <int PS, int PT, int PP, int NR>
+__device__ __forceinline__ void cone_coeffs_block(float2 (*f)[PS * PT * PP], float2 (*tmp)[PS * PT * PP],
+                                                  const float* __restrict__ W, float2* __restrict__ out, int cstride,
+                                                  int nv) {
+    constexpr int P = PS * PT * PP;
+    constexpr int BT = ((P + 31) / 32) * 32;
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int x = threadIdx.x; x < NR * P; x += BT) {
+        const int rl = x / P, m = x - (x / P) * P;
+        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+        const float2* rw = &f[rl][(qa * PT + qb) * PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const float w = Wp[qc * PP + k];
+            a.x = fmaf(w, rw[k].x, a.x);
+            a.y = fmaf(w, rw[k].y, a.y);
+        }
+        tmp[rl][m] = a;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NR * P; x += BT) {
+        const int rl = x / P, m = x - (x / P) * P;
+        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < PT; ++jj) {
+            const float w = Wt[qb * PT + jj];
+            const float2 v = tmp[rl][(qa * PT + jj) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        f[rl][m] = a;
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NR * P; x += BT) {
+        const int rl = x / P, m = x - (x / P) * P;
+        if (rl >= nv) continue;
+        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
+        float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+            const float w = Ws[qa * PS + i];
+            const float2 v = f[rl][(i * PT + qb) * PP + qc];
+            a.x = fmaf(w, v.x, a.x);
+            a.y = fmaf(w, v.y, a.y);
+        }
+        out[(int64_t)rl * cstride + m] = a;
+    }
+}
+
 template <int PS, int PT, int PP, int NR>
 __global__ void k_leaf_f32_multi(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam,
                                  LevelGrid g, const int32_t* __restrict__ startD, const float4* __restrict__ off,
@@ -1252,51 +1308,170 @@ __global__ void k_leaf_f32_multi(const int32_t* __restrict__ cone_box, const int
         for (int r = 0; r < NR; ++r) f[r][n] = acc[r];
     }
     __syncthreads();
-    const float* Ws = W;
-    const float* Wt = W + PS * PS;
-    const float* Wp = Wt + PT * PT;
-    for (int x = threadIdx.x; x < NR * P; x += BT) {
-        const int rl = x / P, m = x - (x / P) * P;
-        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
-        float2 a = make_float2(0.f, 0.f);
-        const float2* rw = &f[rl][(qa * PT + qb) * PP];
+    cone_coeffs_block<PS, PT, PP, NR>(f, tmp, W, coef + ((int64_t)cone * nrhs + rhs0) * cstride, cstride,
+                                      nrhs - rhs0);
+}
+
+// ---- Stokes kernel ------------------------------------------------------------------------
+// The Stokeslet at unit viscosity, S_ij(x,y) = (delta_ij/r + r_i r_j/r^3)/(8 pi) with r = x - y,
+// acting on real force vectors (the Stokes equations are among the kernels Sec. 2 names for
+// Eq. (1)). Its centred factor is the Laplace one, G_0(x,x_k) = 1/(4 pi |x - x_k|), and its
+// analytic factor S(x,x')/G_0(x,x_k) (Eq. (3)) is smooth in the cone variables, so that each
+// velocity component is carried through propagation and interpolation as a kappa = 0 value set.
+// The three real components of force field f occupy reals q = 3f + c of the complex slots, slot
+// q/2, real part for even q: ceil(3 nf / 2) complex sets. Forces in Morton order are SoA,
+// fs[(3 f + c) N + j]; the kernels below take fields in pairs starting at an even field (three
+// complete slots), or the last field of an odd count alone (two slots, the second's imaginary
+// part zero).
+
+// Near field: the tiling and the S-way split of a target's sources of k_near_tile_f32, with the
+// NF force vectors of each staged source held in shared memory next to its position.
+template <int NF>
+__global__ void __launch_bounds__(kNearThreads)
+k_near_stokes_f32(const int4* __restrict__ kD, const int32_t* __restrict__ startD, const int32_t* __restrict__ nnb,
+                  const int32_t* __restrict__ nb, const float4* __restrict__ off, const float* __restrict__ fs,
+                  float2* __restrict__ Is, int64_t N, float inv8piu, int f0) {
+    __shared__ float4 s_p[kNearTile];  // source position in the target box's grid frame; w = source index
+    __shared__ float4 s_f[NF][kNearTile];
+    const int l = blockIdx.x;
+    const int f = f0 + NF * blockIdx.y;
+    const int tid = threadIdx.x;
+    const int t0 = startD[l], m = startD[l + 1] - t0;
+    const int4 kl = kD[l];
+    int S = 1;
+    while (S < 32 && 2 * S * m <= kNearThreads) S *= 2;
+    const int per_pass = kNearThreads / S;
+    const int cnt = nnb[l];
+    for (int base = 0; base < m; base += per_pass) {
+        const int tl = base + tid / S, part = tid % S;
+        const bool active = tl < m;
+        const int i = t0 + (active ? tl : 0);
+        const float4 oi = off[i];
+        float acc[NF][3];
 #pragma unroll
-        for (int k = 0; k < PP; ++k) {
-            const float w = Wp[qc * PP + k];
-            a.x = fmaf(w, rw[k].x, a.x);
-            a.y = fmaf(w, rw[k].y, a.y);
+        for (int r = 0; r < NF; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.f;
+        for (int nq = 0; nq < cnt; ++nq) {
+            const int q = nb[(int64_t)l * kMaxNbr + nq];
+            const int4 kq = kD[q];
+            const float sx = (float)(2 * (kl.x - kq.x)), sy = (float)(2 * (kl.y - kq.y)),
+                        sz = (float)(2 * (kl.z - kq.z));
+            const int j0 = startD[q], j1 = startD[q + 1];
+            for (int tb = j0; tb < j1; tb += kNearTile) {
+                const int nt = min(kNearTile, j1 - tb);
+                __syncthreads();
+                if (tid < nt) {
+                    const int j = tb + tid;
+                    const float4 oj = __ldg(&off[j]);
+                    s_p[tid] = make_float4(oj.x - sx, oj.y - sy, oj.z - sz, __int_as_float(j));
+#pragma unroll
+                    for (int r = 0; r < NF; ++r) {
+                        const float* fr = fs + (int64_t)3 * (f + r) * N + j;
+                        s_f[r][tid] = make_float4(__ldg(fr), __ldg(fr + N), __ldg(fr + 2 * N), 0.f);
+                    }
+                }
+                __syncthreads();
+                if (active) {
+                    for (int k = part; k < nt; k += S) {
+                        const float4 pj = s_p[k];
+                        if (__float_as_int(pj.w) == i) continue;
+                        const float vx = oi.x - pj.x, vy = oi.y - pj.y, vz = oi.z - pj.z;
+                        const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+                        const float rinv = rsqrtf(r2);
+                        const float rinv2 = rinv * rinv;
+#pragma unroll
+                        for (int r = 0; r < NF; ++r) {
+                            const float4 fj = s_f[r][k];
+                            // S f = (f + r (r . f) / r^2) / (8 pi |r|)
+                            const float t = fmaf(vx, fj.x, fmaf(vy, fj.y, vz * fj.z)) * rinv2;
+                            acc[r][0] = fmaf(rinv, fmaf(t, vx, fj.x), acc[r][0]);
+                            acc[r][1] = fmaf(rinv, fmaf(t, vy, fj.y), acc[r][1]);
+                            acc[r][2] = fmaf(rinv, fmaf(t, vz, fj.z), acc[r][2]);
+                        }
+                    }
+                }
+            }
         }
-        tmp[rl][m] = a;
+        for (int o = S / 2; o >= 1; o >>= 1) {  // the S partial sums of a target, fixed order
+#pragma unroll
+            for (int r = 0; r < NF; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], o);
+        }
+        if (active && part == 0) {
+            float2* o = Is + (int64_t)(3 * f / 2) * N + i;
+            o[0] = make_float2(acc[0][0] * inv8piu, acc[0][1] * inv8piu);
+            if constexpr (NF == 2) {
+                o[N] = make_float2(acc[0][2] * inv8piu, acc[1][0] * inv8piu);
+                o[2 * N] = make_float2(acc[1][1] * inv8piu, acc[1][2] * inv8piu);
+            } else {
+                o[N] = make_float2(acc[0][2] * inv8piu, 0.f);
+            }
+        }
+    }
+}
+
+// Leaf level (Algorithm 6) for the Stokeslet: at node y of leaf cone (k, gamma) the analytic
+// factor is S(y, x')/G_0(y, x_k) = (rq/2)(I + w w^T rq^2), w = y_hat - s u (u = (x' - x_k)/h,
+// rq = 1/|w|), then the coefficient transform of the block's complex slots.
+template <int PS, int PT, int PP, int NF>
+__global__ void k_leaf_stokes_f32(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam,
+                                  LevelGrid g, const int32_t* __restrict__ startD, const float4* __restrict__ off,
+                                  const float* __restrict__ fs, int64_t N, float hinv, const float* __restrict__ W,
+                                  float2* __restrict__ coef, int cstride, int nrhs, int f0) {
+    constexpr int P = PS * PT * PP;
+    constexpr int NS = NF == 2 ? 3 : 2;  // complex slots of the block's fields
+    __shared__ float2 v[NS][P], tmp[NS][P];
+    const int cone = blockIdx.x;
+    const int f = f0 + NF * blockIdx.y;
+    const int n = threadIdx.x;
+    const int b = cone_box[cone];
+    if (n < P) {
+        const int gam = cone_gam[cone];
+        const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
+        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+        const float s = g.snode[is * PS + ia];
+        const float st = g.stn[it * PT + ib], ct = g.ctn[it * PT + ib];
+        const float yx = st * g.cpn[ip * PP + ic], yy = st * g.spn[ip * PP + ic], yz = ct;
+        float acc[NF][3];
+#pragma unroll
+        for (int r = 0; r < NF; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.f;
+        for (int j = startD[b]; j < startD[b + 1]; ++j) {
+            const float4 o = __ldg(&off[j]);
+            const float ux = o.x * hinv, uy = o.y * hinv, uz = o.z * hinv;
+            const float wx = fmaf(-s, ux, yx), wy = fmaf(-s, uy, yy), wz = fmaf(-s, uz, yz);
+            const float q = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+            const float rq = rsqrtf(q);
+            const float rq2 = rq * rq;
+#pragma unroll
+            for (int r = 0; r < NF; ++r) {
+                const float* fr = fs + (int64_t)3 * (f + r) * N + j;
+                const float fx = __ldg(fr), fy = __ldg(fr + N), fz = __ldg(fr + 2 * N);
+                const float t = fmaf(wx, fx, fmaf(wy, fy, wz * fz)) * rq2;
+                acc[r][0] = fmaf(rq, fmaf(t, wx, fx), acc[r][0]);
+                acc[r][1] = fmaf(rq, fmaf(t, wy, fy), acc[r][1]);
+                acc[r][2] = fmaf(rq, fmaf(t, wz, fz), acc[r][2]);
+            }
+        }
+        v[0][n] = make_float2(0.5f * acc[0][0], 0.5f * acc[0][1]);
+        if constexpr (NF == 2) {
+            v[1][n] = make_float2(0.5f * acc[0][2], 0.5f * acc[1][0]);
+            v[2][n] = make_float2(0.5f * acc[1][1], 0.5f * acc[1][2]);
+        } else {
+            v[1][n] = make_float2(0.5f * acc[0][2], 0.f);
+        }
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < NR * P; x += BT) {
-        const int rl = x / P, m = x - (x / P) * P;
-        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
-        float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int jj = 0; jj < PT; ++jj) {
-            const float w = Wt[qb * PT + jj];
-            const float2 v = tmp[rl][(qa * PT + jj) * PP + qc];
-            a.x = fmaf(w, v.x, a.x);
-            a.y = fmaf(w, v.y, a.y);
-        }
-        f[rl][m] = a;
-    }
-    __syncthreads();
-    for (int x = threadIdx.x; x < NR * P; x += BT) {
-        const int rl = x / P, m = x - (x / P) * P;
-        if (rhs0 + rl >= nrhs) continue;
-        const int qc = m % PP, qb = (m / PP) % PT, qa = m / (PP * PT);
-        float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < PS; ++i) {
-            const float w = Ws[qa * PS + i];
-            const float2 v = f[rl][(i * PT + qb) * PP + qc];
-            a.x = fmaf(w, v.x, a.x);
-            a.y = fmaf(w, v.y, a.y);
-        }
-        coef[((int64_t)cone * nrhs + rhs0 + rl) * cstride + m] = a;
-    }
+    cone_coeffs_block<PS, PT, PP, NS>(v, tmp, W, coef + ((int64_t)cone * nrhs + 3 * f / 2) * cstride, cstride, NS);
+}
+
+// Velocities back to the caller's order: real q of the slots -> out[q][perm[i]].
+__global__ void k_perm_out_stokes(const float2* __restrict__ Is, const int32_t* __restrict__ perm, int64_t N,
+                                  float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int q = blockIdx.y;
+    const float2 v = Is[(int64_t)(q >> 1) * N + i];
+    out[(int64_t)q * N + perm[i]] = (q & 1) ? v.y : v.x;
 }
 
 // ---- driver -------------------------------------------------------------------------------
@@ -1316,40 +1491,19 @@ void for_each_slice(const Plan& p, int d, F&& launch) {
     }
 }
 
+// Levels D..3 of the many-density path: interpolation to the targets of level d (Algorithm 8),
+// then propagation into level d-1 (Algorithm 7) on the tensor cores.
 template <int NT, int PS, int PT, int PP>
-void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
+void sweep_levels_mma(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mask) {
     constexpr int P = PS * PT * PP;
-    constexpr int BT = ((P + 31) / 32) * 32;
     constexpr int NR = 4 * NT;
-    constexpr int NRB = 8;  // densities per near-field / leaf block
     const int64_t N = p.N;
     const int D = p.D;
-    const double u = p.u;
     Level& LD = p.L[D];
-    const float ku = (float)(p.kappa * u);
-    const float inv4piu = (float)(1.0 / (4.0 * M_PI * u));
-    float2* as = (float2*)p.a_s;
-    float2* Is = (float2*)p.I_s;
+    const float ku = (float)(p.kappa * p.u);
+    const float inv4piu = (float)(1.0 / (4.0 * M_PI * p.u));
     const dim3 gN(grid_for(N, kThreads), nrhs);
     const unsigned rb = (unsigned)((nrhs + NR - 1) / NR);
-    const unsigned rb8 = (unsigned)((nrhs + NRB - 1) / NRB);
-    {
-        TimedScope ts_(TK_PERM, s);
-        IFGF_LAUNCH(k_perm_in<float2>, gN, kThreads, 0, s, (const float2*)dens, p.perm, N, as);
-    }
-    if (near) {
-        TimedScope ts_(TK_NEAR, s);
-        IFGF_LAUNCH(k_near_f32_multi<NRB>, dim3(grid_for(N, kThreads), rb8), kThreads, 0, s, N, LD.pbox, LD.k, LD.start,
-                    LD.nnb, LD.nb, p.off, as, Is, ku, inv4piu, nrhs);
-    } else {
-        IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * nrhs, s));
-    }
-    if (LD.nc > 0) {
-        TimedScope ts_(TK_LEAF, s);
-        IFGF_LAUNCH((k_leaf_f32_multi<PS, PT, PP, NRB>), dim3((unsigned)LD.nc, rb8), BT, 0, s, LD.cone_box,
-                    LD.cone_gam, LD.g, LD.start, p.off, as, N, (float)(p.kappa * LD.g.h64), 1.0f / LD.g.hg, p.Wf,
-                    (float2*)level_coef(p, D, nrhs), p.cstride, nrhs);
-    }
     for (int d = D; d >= 3; --d) {
         Level& L = p.L[d];
         const int sh = D - d;
@@ -1380,6 +1534,41 @@ void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStre
             });
         }
     }
+}
+
+template <int NT, int PS, int PT, int PP>
+void run_apply_multi_nt(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
+    constexpr int P = PS * PT * PP;
+    constexpr int BT = ((P + 31) / 32) * 32;
+    constexpr int NRB = 8;  // densities per near-field / leaf block
+    const int64_t N = p.N;
+    const int D = p.D;
+    const double u = p.u;
+    Level& LD = p.L[D];
+    const float ku = (float)(p.kappa * u);
+    const float inv4piu = (float)(1.0 / (4.0 * M_PI * u));
+    float2* as = (float2*)p.a_s;
+    float2* Is = (float2*)p.I_s;
+    const dim3 gN(grid_for(N, kThreads), nrhs);
+    const unsigned rb8 = (unsigned)((nrhs + NRB - 1) / NRB);
+    {
+        TimedScope ts_(TK_PERM, s);
+        IFGF_LAUNCH(k_perm_in<float2>, gN, kThreads, 0, s, (const float2*)dens, p.perm, N, as);
+    }
+    if (near) {
+        TimedScope ts_(TK_NEAR, s);
+        IFGF_LAUNCH(k_near_f32_multi<NRB>, dim3(grid_for(N, kThreads), rb8), kThreads, 0, s, N, LD.pbox, LD.k, LD.start,
+                    LD.nnb, LD.nb, p.off, as, Is, ku, inv4piu, nrhs);
+    } else {
+        IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * nrhs, s));
+    }
+    if (LD.nc > 0) {
+        TimedScope ts_(TK_LEAF, s);
+        IFGF_LAUNCH((k_leaf_f32_multi<PS, PT, PP, NRB>), dim3((unsigned)LD.nc, rb8), BT, 0, s, LD.cone_box,
+                    LD.cone_gam, LD.g, LD.start, p.off, as, N, (float)(p.kappa * LD.g.h64), 1.0f / LD.g.hg, p.Wf,
+                    (float2*)level_coef(p, D, nrhs), p.cstride, nrhs);
+    }
+    sweep_levels_mma<NT, PS, PT, PP>(p, nrhs, Is, s, mask);
     {
         TimedScope ts_(TK_PERM, s);
         IFGF_LAUNCH(k_perm_out<float2>, gN, kThreads, 0, s, Is, p.perm, N, (float2*)out);
@@ -1398,6 +1587,69 @@ void run_apply_multi(Plan& p, const void* dens, int nrhs, void* out, cudaStream_
     } else {
         fail(IFGF_ERR_UNSUPPORTED, "tensor-core path built for orders (3,5,5) only");
     }
+}
+
+// Levels D..3 of the mixed path with few densities: interpolation to the targets of level d
+// (Algorithm 8), then propagation into level d-1 (Algorithm 7), from node tables where the
+// level has them.
+template <int PS, int PT, int PP>
+void sweep_levels_f32(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mask) {
+    const int64_t N = p.N;
+    const int D = p.D;
+    Level& LD = p.L[D];
+    const float ku = (float)(p.kappa * p.u);
+    const float inv4piu = (float)(1.0 / (4.0 * M_PI * p.u));
+    const dim3 gN(grid_for(N, kThreads), nrhs);
+    for (int d = D; d >= 3; --d) {
+        Level& L = p.L[d];
+        const int sh = D - d;
+        if ((mask >> d) & 1) {
+            TimedScope ts_(TK_INTERP, s);
+            IFGF_LAUNCH((k_interp_f32<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs, L.cs,
+                        p.off, L.cmap(), L.g, (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu, Is,
+                        p.cstride, nrhs, p.d_status);
+        }
+        if (d == 3) break;
+        Level& Lp = p.L[d - 1];
+        const float2* cc = (const float2*)level_coef(p, d, nrhs);
+        float2* cp = (float2*)level_coef(p, d - 1, nrhs);
+        const int64_t cone = (int64_t)nrhs * p.cstride;
+        if (Lp.nc > 0 && Lp.n_gam > 0 && PS * PT * PP <= 75) {  // tables are built for (3,5,5) only
+            TimedScope ts_(TK_PROP, s);
+            constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
+                          TP = PS * PT * PP <= 75 ? PP : 5;
+            for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP>), dim3((unsigned)((n + kWarpCones - 1) / kWarpCones), nrhs),
+                            32 * kWarpCones, 0, s, n, Lp.cone_box + lo, Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k,
+                            L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, Lp.tab_nseg,
+                            Lp.tab_seg, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
+            });
+        } else if (Lp.nc > 0) {
+            TimedScope ts_(TK_PROP, s);
+            for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((n + kPropCones - 1) / kPropCones), nrhs),
+                            kPropThreads, 0, s, n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k,
+                            L.cmap(), L.g, cc, cp + lo * cone, sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
+            });
+        }
+    }
+}
+
+// The mixed-precision level sweep for nrhs value sets: tensor-core kernels from kMmaMinRhs sets on.
+template <int PS, int PT, int PP>
+void sweep_levels_mixed(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mask) {
+    if constexpr (PS == 3 && PT == 5 && PP == 5) {
+        if (nrhs >= kMmaMinRhs) {
+            if (nrhs <= 8)
+                sweep_levels_mma<2, PS, PT, PP>(p, nrhs, Is, s, mask);
+            else if (nrhs <= 16)
+                sweep_levels_mma<4, PS, PT, PP>(p, nrhs, Is, s, mask);
+            else
+                sweep_levels_mma<8, PS, PT, PP>(p, nrhs, Is, s, mask);
+            return;
+        }
+    }
+    sweep_levels_f32<PS, PT, PP>(p, nrhs, Is, s, mask);
 }
 
 template <int PS, int PT, int PP>
@@ -1438,40 +1690,7 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                             LD.cone_gam, LD.g, LD.start, p.off, as, N, kh, 1.0f / LD.g.hg, p.Wf,
                             (float2*)level_coef(p, D, nrhs), p.cstride, nrhs);
             }
-        for (int d = D; d >= 3; --d) {
-            Level& L = p.L[d];
-            const int sh = D - d;
-            if ((mask >> d) & 1)
-                {
-                    TimedScope ts_(TK_INTERP, s);
-                    IFGF_LAUNCH((k_interp_f32<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs,
-                                L.cs, p.off, L.cmap(), L.g, (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu,
-                                Is, p.cstride, nrhs, p.d_status);
-                }
-            if (d == 3) break;
-            Level& Lp = p.L[d - 1];
-            const float2* cc = (const float2*)level_coef(p, d, nrhs);
-            float2* cp = (float2*)level_coef(p, d - 1, nrhs);
-            const int64_t cone = (int64_t)nrhs * p.cstride;
-            if (Lp.nc > 0 && Lp.n_gam > 0 && PS * PT * PP <= 75) {  // tables are built for (3,5,5) only
-                TimedScope ts_(TK_PROP, s);
-                constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
-                              TP = PS * PT * PP <= 75 ? PP : 5;
-                for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                    IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP>), dim3((unsigned)((n + kWarpCones - 1) / kWarpCones), nrhs),
-                                32 * kWarpCones, 0, s, n, Lp.cone_box + lo, Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k,
-                                L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, Lp.tab_nseg,
-                                Lp.tab_seg, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
-                });
-            } else if (Lp.nc > 0) {
-                TimedScope ts_(TK_PROP, s);
-                for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                    IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((n + kPropCones - 1) / kPropCones), nrhs),
-                                kPropThreads, 0, s, n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k,
-                                L.cmap(), L.g, cc, cp + lo * cone, sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
-                });
-            }
-        }
+        sweep_levels_f32<PS, PT, PP>(p, nrhs, Is, s, mask);
         {
             TimedScope ts_(TK_PERM, s);
             IFGF_LAUNCH(k_perm_out<float2>, gN, kThreads, 0, s, Is, p.perm, N, (float2*)out);
@@ -1529,6 +1748,54 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
     }
 }
 
+// Stokes apply of nf force fields ([nf][3][N] float, caller's order) into velocities of the
+// same layout: Stokes near field and leaf level, then the kappa = 0 level sweep on the
+// ceil(3 nf / 2) complex slots.
+template <int PS, int PT, int PP>
+void run_apply_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStream_t s, bool near, int64_t mask) {
+    constexpr int P = PS * PT * PP;
+    constexpr int BT = ((P + 31) / 32) * 32;
+    const int64_t N = p.N;
+    const int D = p.D;
+    Level& LD = p.L[D];
+    const int nreal = 3 * nf, slots = (nreal + 1) / 2, pairs = nf / 2;
+    float* fs = (float*)p.a_s;
+    float2* Is = (float2*)p.I_s;
+    const float inv8piu = (float)(1.0 / (8.0 * M_PI * p.u));
+    const dim3 gR(grid_for(N, kThreads), nreal);
+    {
+        TimedScope ts_(TK_PERM, s);
+        IFGF_LAUNCH(k_perm_in<float>, gR, kThreads, 0, s, forces, p.perm, N, fs);
+    }
+    if (near) {
+        TimedScope ts_(TK_NEAR, s);
+        if (pairs > 0)
+            IFGF_LAUNCH(k_near_stokes_f32<2>, dim3((unsigned)LD.n, pairs), kNearThreads, 0, s, LD.k, LD.start, LD.nnb,
+                        LD.nb, p.off, fs, Is, N, inv8piu, 0);
+        if (nf & 1)
+            IFGF_LAUNCH(k_near_stokes_f32<1>, dim3((unsigned)LD.n, 1), kNearThreads, 0, s, LD.k, LD.start, LD.nnb,
+                        LD.nb, p.off, fs, Is, N, inv8piu, nf - 1);
+    } else {
+        IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * slots, s));
+    }
+    if (LD.nc > 0) {
+        TimedScope ts_(TK_LEAF, s);
+        float2* cD = (float2*)level_coef(p, D, slots);
+        const float hinv = 1.0f / LD.g.hg;
+        if (pairs > 0)
+            IFGF_LAUNCH((k_leaf_stokes_f32<PS, PT, PP, 2>), dim3((unsigned)LD.nc, pairs), BT, 0, s, LD.cone_box,
+                        LD.cone_gam, LD.g, LD.start, p.off, fs, N, hinv, p.Wf, cD, p.cstride, slots, 0);
+        if (nf & 1)
+            IFGF_LAUNCH((k_leaf_stokes_f32<PS, PT, PP, 1>), dim3((unsigned)LD.nc, 1), BT, 0, s, LD.cone_box,
+                        LD.cone_gam, LD.g, LD.start, p.off, fs, N, hinv, p.Wf, cD, p.cstride, slots, nf - 1);
+    }
+    sweep_levels_mixed<PS, PT, PP>(p, slots, Is, s, mask);
+    {
+        TimedScope ts_(TK_PERM, s);
+        IFGF_LAUNCH(k_perm_out_stokes, gR, kThreads, 0, s, Is, p.perm, N, vel);
+    }
+}
+
 }  // namespace
 
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
@@ -1542,6 +1809,25 @@ void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, 
             run_apply<3, 5, 5>(p, d, nb, o, s, near, mask);
         else if (p.Ps == 5 && p.Pt == 7 && p.Pp == 7)
             run_apply<5, 7, 7>(p, d, nb, o, s, near, mask);
+        else
+            fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
+    }
+}
+
+void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStream_t s, bool near, int64_t mask) {
+    // force fields in blocks whose ceil(3 nfb / 2) slots fit the arena's rhs_block value sets;
+    // an even block size keeps every block but the last free of a half-empty slot
+    int nfb = std::min(2 * p.rhs_block / 3, 21844);  // 3 nfb real sets fit a grid's y extent
+    if (nfb >= 2) nfb &= ~1;
+    if (nfb < 1) fail(IFGF_ERR_UNSUPPORTED, "the coefficient arena holds fewer than two value sets");
+    for (int f0 = 0; f0 < nf; f0 += nfb) {
+        const int nb = std::min(nfb, nf - f0);
+        const float* f = forces + (size_t)3 * f0 * p.N;
+        float* u = vel + (size_t)3 * f0 * p.N;
+        if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
+            run_apply_stokes<3, 5, 5>(p, f, nb, u, s, near, mask);
+        else if (p.Ps == 5 && p.Pt == 7 && p.Pp == 7)
+            run_apply_stokes<5, 7, 7>(p, f, nb, u, s, near, mask);
         else
             fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
     }

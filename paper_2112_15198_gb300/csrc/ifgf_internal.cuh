@@ -262,6 +262,7 @@ inline char* level_coef(const Plan& p, int d, int nb) {
 }
 void destroy_plan(Plan& p);
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask);
+void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStream_t s, bool near, int64_t mask);
 
 // =========================================================================================
 // Device helpers

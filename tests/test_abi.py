@@ -67,6 +67,7 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert b"orders" in lib.ifgf_last_error()
     assert lib.ifgf_plan_destroy(None) == 0
     assert lib.ifgf_apply(None, None, 1, None, None) == 1
+    assert lib.ifgf_apply_stokes(None, None, 1, None, None) == 1
 
 
 def test_library_links_no_torch(lib):
