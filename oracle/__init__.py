@@ -12,6 +12,9 @@ O2  ``Plan``: the plain CPU IFGF (tree, cousins, relevant cones of Eq. (4),
 S1  ``stokes_direct_sum``: Eq. (1) with the Stokeslet (Stokes Green tensor at
     unit viscosity) acting on real force vectors, pair by pair in FP64.
 S2  ``Plan.apply_stokes``: the O2 IFGF for the Stokeslet on a kappa = 0 plan.
+E1  ``elastic_direct_sum``: Eq. (1) with Kelvin's solution of linear elasticity
+    (shear modulus mu, Poisson ratio nu), pair by pair in FP64.
+E2  ``Plan.apply_elastic``: the O2 IFGF for Kelvin's solution on a kappa = 0 plan.
 
 Parity unpinned: none of the functions here lacks a pin; see ``tests/test_oracle_*``.
 """
@@ -77,6 +80,11 @@ def _load():
         lib.orc_stokes_direct_sum.restype = None
         lib.orc_apply_stokes.argtypes = [c_vp, c_int, c_vp, c_vp, c_int, c_i64]
         lib.orc_apply_stokes.restype = c_int
+        lib.orc_elastic_direct_sum.argtypes = [c_i64, c_vp, c_vp, c_vp, c_dbl, c_dbl, c_int, c_vp, c_i64, c_vp,
+                                               c_vp]
+        lib.orc_elastic_direct_sum.restype = None
+        lib.orc_apply_elastic.argtypes = [c_vp, c_dbl, c_dbl, c_int, c_vp, c_vp, c_int, c_i64]
+        lib.orc_apply_elastic.restype = c_int
         lib.orc_get.argtypes = [c_vp, c_int, c_int, c_vp]
         lib.orc_get.restype = c_i64
         lib.orc_info.argtypes = [c_vp, c_vp, c_vp]
@@ -138,6 +146,22 @@ def stokes_direct_sum(points: np.ndarray, forces: np.ndarray, tgt=None) -> np.nd
     out = np.zeros((nf, 3, t.shape[0]), dtype=np.float64)
     x, y, z = (np.ascontiguousarray(pts[i]) for i in range(3))
     lib.orc_stokes_direct_sum(n, _ptr(x), _ptr(y), _ptr(z), nf, _ptr(f), t.shape[0], _ptr(t), _ptr(out))
+    return out
+
+
+def elastic_direct_sum(points: np.ndarray, forces: np.ndarray, mu: float, nu: float, tgt=None) -> np.ndarray:
+    """E1: u_i(x_l) = sum_{m != l} sum_j K_ij(x_l, x_m) f_j(x_m), K Kelvin's solution,
+    K_ij = ((3 - 4 nu) delta_ij/r + r_i r_j/r^3)/(16 pi mu (1 - nu)); layouts as stokes_direct_sum."""
+    lib = _load()
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n = pts.shape[1]
+    f = np.ascontiguousarray(np.asarray(forces, dtype=np.float64).reshape(-1, 3, n))
+    nf = f.shape[0]
+    t = np.arange(n, dtype=np.int64) if tgt is None else np.ascontiguousarray(tgt, dtype=np.int64)
+    out = np.zeros((nf, 3, t.shape[0]), dtype=np.float64)
+    x, y, z = (np.ascontiguousarray(pts[i]) for i in range(3))
+    lib.orc_elastic_direct_sum(n, _ptr(x), _ptr(y), _ptr(z), float(mu), float(nu), nf, _ptr(f), t.shape[0],
+                               _ptr(t), _ptr(out))
     return out
 
 
@@ -243,6 +267,17 @@ class Plan:
         st = self._lib.orc_apply_stokes(self._h, f.shape[0], _ptr(f), _ptr(out), 1 if near else 0, int(level_mask))
         if st != 0:
             raise OracleError(f"orc_apply_stokes failed with status {st}")
+        return out
+
+    def apply_elastic(self, forces: np.ndarray, mu: float, nu: float, near: bool = True,
+                      level_mask: int = -1) -> np.ndarray:
+        """FP64 IFGF apply of Kelvin's solution (kappa = 0 plans), layouts as apply_stokes."""
+        f = np.ascontiguousarray(np.asarray(forces, dtype=np.float64).reshape(-1, 3, self.N))
+        out = np.zeros_like(f)
+        st = self._lib.orc_apply_elastic(self._h, float(mu), float(nu), f.shape[0], _ptr(f), _ptr(out),
+                                         1 if near else 0, int(level_mask))
+        if st != 0:
+            raise OracleError(f"orc_apply_elastic failed with status {st}")
         return out
 
     def work(self) -> dict:

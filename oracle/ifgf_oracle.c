@@ -18,6 +18,8 @@
  *   S1  orc_stokes_direct_sum   Eq. (1) with the Stokes Green tensor (the Stokeslet),
  *                           one of the kernels Sec. 2 names, FP64, compensated sums.
  *   S2  orc_apply_stokes    the same IFGF steps for the Stokeslet on a kappa = 0 plan.
+ *   E1  orc_elastic_direct_sum  Eq. (1) with Kelvin's solution of linear elasticity.
+ *   E2  orc_apply_elastic   the IFGF steps for Kelvin's solution on a kappa = 0 plan.
  *
  * The paper defers the numerical details of IFGF (analytic factor, the
  * singularity-resolving radial variable, interpolation nodes, cone counts) to
@@ -46,7 +48,11 @@
  *     vectors f_m; its centred factor is the Laplace one, G_0(x,x_k) = 1/(4 pi |x-x_k|),
  *     and its analytic factor S_ij(x,x')/G_0(x,x_k) (Eq. (3) with a matrix-valued G),
  *     so that propagation and interpolation are those of the kappa = 0 kernel applied
- *     to each of the three velocity components.
+ *     to each of the three velocity components;
+ *   - elasticity kernel: Kelvin's solution for a point force in an infinite isotropic solid
+ *     with shear modulus mu and Poisson ratio nu,
+ *     K_ij(x,y) = ((3-4nu) delta_ij/r + (x_i-y_i)(x_j-y_j)/r^3)/(16 pi mu (1-nu)),
+ *     factored like the Stokeslet.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared  (no -ffast-math:
  * classification relies on IEEE single precision without contraction).
@@ -127,13 +133,29 @@ static void stokeslet(const double* v, double S[3][3]) {
             S[i][j] = ((i == j ? 1.0 / r : 0.0) + v[i] * v[j] / (r * r * r)) / (8.0 * M_PI);
 }
 
-/*
- * S1: u_i(x_l) = sum_{m != l} sum_j S_ij(x_l, x_m) f_j(x_m)  (Eq. (1) with the Stokeslet),
- * at the M target indices tgt[], for every force field s < nf.  f is [nf][3][N] real,
- * out is [nf][3][M].
- */
-void orc_stokes_direct_sum(int64_t N, const double* x, const double* y, const double* z, int nf,
-                           const double* f, int64_t M, const int64_t* tgt, double* out) {
+/* Kelvin's solution of the Navier equations of linear elasticity for the separation v = x - y
+ * (displacement at x due to a unit point force at y; shear modulus mu, Poisson ratio nu):
+ * K_ij = ((3 - 4 nu) delta_ij / r + v_i v_j / r^3) / (16 pi mu (1 - nu)). */
+static void kelvinlet(const double* v, double mu, double nu, double S[3][3]) {
+    const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            S[i][j] = ((i == j ? (3.0 - 4.0 * nu) / r : 0.0) + v[i] * v[j] / (r * r * r)) /
+                      (16.0 * M_PI * mu * (1.0 - nu));
+}
+
+/* Green tensor of kind 1 (Stokeslet) or 2 (Kelvin's solution with mu, nu). */
+static void green_tensor(int kind, double mu, double nu, const double* v, double S[3][3]) {
+    if (kind == 1)
+        stokeslet(v, S);
+    else
+        kelvinlet(v, mu, nu, S);
+}
+
+/* u_i(x_l) = sum_{m != l} sum_j T_ij(x_l, x_m) f_j(x_m) for the Green tensor T of `kind`. */
+static void tensor_direct_sum(int kind, double mu, double nu, int64_t N, const double* x, const double* y,
+                              const double* z, int nf, const double* f, int64_t M, const int64_t* tgt,
+                              double* out) {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < M; ++t) {
         const int64_t l = tgt[t];
@@ -142,7 +164,7 @@ void orc_stokes_direct_sum(int64_t N, const double* x, const double* y, const do
             if (m == l) continue;
             const double v[3] = {x[l] - x[m], y[l] - y[m], z[l] - z[m]};
             double S[3][3];
-            stokeslet(v, S);
+            green_tensor(kind, mu, nu, v, S);
             for (int q = 0; q < nf; ++q)
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j < 3; ++j)
@@ -151,6 +173,22 @@ void orc_stokes_direct_sum(int64_t N, const double* x, const double* y, const do
         for (int c = 0; c < 3 * nf; ++c) out[(int64_t)c * M + t] = acc[c].s + acc[c].c;
         free(acc);
     }
+}
+
+/*
+ * S1: u_i(x_l) = sum_{m != l} sum_j S_ij(x_l, x_m) f_j(x_m)  (Eq. (1) with the Stokeslet),
+ * at the M target indices tgt[], for every force field s < nf.  f is [nf][3][N] real,
+ * out is [nf][3][M].
+ */
+void orc_stokes_direct_sum(int64_t N, const double* x, const double* y, const double* z, int nf,
+                           const double* f, int64_t M, const int64_t* tgt, double* out) {
+    tensor_direct_sum(1, 1.0, 0.5, N, x, y, z, nf, f, M, tgt, out);
+}
+
+/* E1: the same with Kelvin's solution (shear modulus mu, Poisson ratio nu). */
+void orc_elastic_direct_sum(int64_t N, const double* x, const double* y, const double* z, double mu, double nu,
+                            int nf, const double* f, int64_t M, const int64_t* tgt, double* out) {
+    tensor_direct_sum(2, mu, nu, N, x, y, z, nf, f, M, tgt, out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -787,14 +825,15 @@ int orc_has_duplicates(const orc_plan* p) {
  * level-d cousin interpolations (all levels: ~0).
  */
 /*
- * The IFGF apply on nrhs channels.  Helmholtz (stokes = 0): channel q is density vector q.
- * Stokes (stokes = 1, kappa = 0): channel 3s+j holds component j of force field s (real
- * values in complex storage); the near field and the leaf evaluation contract the
- * Stokeslet with the force vector, everything after the leaf level acts on each channel
- * alone, as it does for the kappa = 0 kernel.
+ * The IFGF apply on nrhs channels.  Helmholtz (kind = 0): channel q is density vector q.
+ * Green tensors (kind 1 Stokeslet, kind 2 Kelvin's solution with mu, nu; kappa = 0): channel
+ * 3s+j holds component j of force field s (real values in complex storage); the near field and
+ * the leaf evaluation contract the tensor with the force vector, everything after the leaf
+ * level acts on each channel alone, as it does for the kappa = 0 kernel.
  */
-static int apply_impl(orc_plan* p, int stokes, int nrhs, const cplx* a, cplx* out, int near,
+static int apply_impl(orc_plan* p, int kind, double mu, double nu, int nrhs, const cplx* a, cplx* out, int near,
                       int64_t level_mask) {
+    const int stokes = kind != 0;
     const int64_t N = p->N;
     const int D = p->D, P = p->P, Ps = p->Ps, Pt = p->Pt, Pp = p->Pp;
     const double kappa = p->kappa;
@@ -821,7 +860,7 @@ static int apply_impl(orc_plan* p, int stokes, int nrhs, const cplx* a, cplx* ou
                         if (stokes) {
                             const double v[3] = {dx, dy, dz};
                             double S[3][3];
-                            stokeslet(v, S);
+                            green_tensor(kind, mu, nu, v, S);
                             for (int q = 0; q < nrhs / 3; ++q)
                                 for (int c = 0; c < 3; ++c)
                                     for (int e = 0; e < 3; ++e)
@@ -861,7 +900,7 @@ static int apply_impl(orc_plan* p, int stokes, int nrhs, const cplx* a, cplx* ou
                             /* analytic factor S_ij(y, x') / G_0(y, x_k), G_0(y, x_k) = 1/(4 pi r) */
                             const double v[3] = {dx, dy, dz};
                             double S[3][3];
-                            stokeslet(v, S);
+                            green_tensor(kind, mu, nu, v, S);
                             for (int q = 0; q < nrhs / 3; ++q)
                                 for (int c = 0; c < 3; ++c)
                                     for (int e = 0; e < 3; ++e)
@@ -971,22 +1010,34 @@ static int apply_impl(orc_plan* p, int stokes, int nrhs, const cplx* a, cplx* ou
 }
 
 int orc_apply(orc_plan* p, int nrhs, const cplx* a, cplx* out, int near, int64_t level_mask) {
-    return apply_impl(p, 0, nrhs, a, out, near, level_mask);
+    return apply_impl(p, 0, 0.0, 0.0, nrhs, a, out, near, level_mask);
 }
 
-/* S2: u = IFGF approximation of S1 at every point; f and u are [nf][3][N] real in the
- * caller's point order.  The plan must have kappa = 0. */
-int orc_apply_stokes(orc_plan* p, int nf, const double* f, double* u, int near, int64_t level_mask) {
+static int apply_tensor(orc_plan* p, int kind, double mu, double nu, int nf, const double* f, double* u, int near,
+                        int64_t level_mask) {
     if (p->kappa != 0.0 || nf < 1) return ORC_ERR_ARG;
     const int64_t n = (int64_t)3 * nf * p->N;
     cplx* a = (cplx*)xcalloc((size_t)n, sizeof(cplx));
     cplx* o = (cplx*)xcalloc((size_t)n, sizeof(cplx));
     for (int64_t i = 0; i < n; ++i) a[i] = f[i];
-    int st = apply_impl(p, 1, 3 * nf, a, o, near, level_mask);
+    int st = apply_impl(p, kind, mu, nu, 3 * nf, a, o, near, level_mask);
     for (int64_t i = 0; i < n; ++i) u[i] = creal(o[i]);
     free(a);
     free(o);
     return st;
+}
+
+/* S2: u = IFGF approximation of S1 at every point; f and u are [nf][3][N] real in the
+ * caller's point order.  The plan must have kappa = 0. */
+int orc_apply_stokes(orc_plan* p, int nf, const double* f, double* u, int near, int64_t level_mask) {
+    return apply_tensor(p, 1, 1.0, 0.5, nf, f, u, near, level_mask);
+}
+
+/* E2: the IFGF approximation of E1, as orc_apply_stokes. */
+int orc_apply_elastic(orc_plan* p, double mu, double nu, int nf, const double* f, double* u, int near,
+                      int64_t level_mask) {
+    if (!(mu > 0.0) || !(nu > -1.0) || !(nu <= 0.5)) return ORC_ERR_ARG;
+    return apply_tensor(p, 2, mu, nu, nf, f, u, near, level_mask);
 }
 
 /* ------------------------------------------------------------------------- */
