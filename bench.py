@@ -74,8 +74,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--nrhs", type=int, default=0,
                     help="densities (force fields for --kernel stokes) per apply; 0: the workload's own count")
-    ap.add_argument("--kernel", default="helmholtz", choices=["helmholtz", "stokes"],
-                    help="stokes: the Stokeslet on the workload's points (kappa = 0, real force fields)")
+    ap.add_argument("--kernel", default="helmholtz", choices=["helmholtz", "stokes", "elastic"],
+                    help="stokes: the Stokeslet on the workload's points (kappa = 0, real force fields); "
+                         "elastic: Kelvin's solution with mu = 1, nu = 0.3 on the same inputs")
     return ap.parse_args()
 
 
@@ -228,12 +229,11 @@ def run_reference(args, ws, rank):
         prob.exact(oracle, pts, dens, tg)
         times.append(time.perf_counter() - t0)
     value = m * w.nrhs / statistics.median(times)
-    what = "the Stokeslet sum" if prob.stokes else "Eq. (1)"
-    sample = f"direct sum of {what} at {m} of the {w.n} targets per step (FP64, OpenMP)"
+    sample = f"direct sum of {prob.what()} at {m} of the {w.n} targets per step (FP64, OpenMP)"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config_of(w, args.precision, None, prob.stokes),
+           "config": config_of(w, args.precision, None, prob.kind),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -243,16 +243,20 @@ def workload_of(args):
     w = W.make(args.workload)
     if args.nrhs > 0:
         w = dataclasses.replace(w, nrhs=args.nrhs)
-    if args.kernel == "stokes":
+    if args.kernel != "helmholtz":
         w = dataclasses.replace(w, wavelengths=0.0)
     return w
+
+
+ELASTIC_MU, ELASTIC_NU = 1.0, 0.3
 
 
 class Problem:
     """The apply of one kernel on a workload: inputs, plan and oracle reference."""
 
     def __init__(self, args, w):
-        self.w, self.stokes, self.precision = w, args.kernel == "stokes", args.precision
+        self.w, self.kind, self.precision = w, args.kernel, args.precision
+        self.stokes = args.kernel != "helmholtz"  # a Green tensor acting on real force fields
         # complex value sets carried through the levels
         self.sets = (3 * w.nrhs + 1) // 2 if self.stokes else w.nrhs
 
@@ -274,22 +278,31 @@ class Problem:
         return ifgf.Plan(P, self.w.kappa, precision=self.precision, max_nrhs=self.sets)
 
     def apply(self, plan, A, out):
-        if self.stokes:
+        if self.kind == "stokes":
             plan.apply_stokes(A, out)
+        elif self.kind == "elastic":
+            plan.apply_elastic(A, out, ELASTIC_MU, ELASTIC_NU)
         else:
             plan.apply(A, out)
 
     def exact(self, oracle, pts, host, tgt):
-        if self.stokes:
+        if self.kind == "stokes":
             return oracle.stokes_direct_sum(pts, host, tgt)
+        if self.kind == "elastic":
+            return oracle.elastic_direct_sum(pts, host, ELASTIC_MU, ELASTIC_NU, tgt)
         return oracle.direct_sum(pts, self.w.kappa, host, tgt)
 
+    def what(self):
+        return {"stokes": "the Stokeslet sum", "elastic": "the Kelvin-solution sum"}.get(self.kind, "Eq. (1)")
 
-def config_of(w, precision, D, stokes=False):
+
+def config_of(w, precision, D, kind="helmholtz"):
     body = ("Fibonacci sphere, unit diameter" if w.geometry == "sphere"
             else f"spheroid with semi-axes ({w.axes[0]:g}, {w.axes[0]:g}, {w.axes[1]:g})")
-    if stokes:
-        what = (f"{w.name} points: {body}, Stokeslet (unit viscosity), N = {w.n}, nrhs = {w.nrhs} force fields "
+    if kind != "helmholtz":
+        green = ("Stokeslet (unit viscosity)" if kind == "stokes"
+                 else f"Kelvin's solution (mu = {ELASTIC_MU:g}, nu = {ELASTIC_NU:g})")
+        what = (f"{w.name} points: {body}, {green}, N = {w.n}, nrhs = {w.nrhs} force fields "
                 f"iid U[-1,1]^3")
     else:
         what = (f"{w.name}: {body}, {w.wavelengths:g} wavelengths (kappa = 2 pi x {w.wavelengths:g}), N = {w.n}, "
@@ -460,7 +473,7 @@ def main():
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-           "config": config_of(w, args.precision, D, prob.stokes),
+           "config": config_of(w, args.precision, D, prob.kind),
            "e2e": {"value": whole_job_value(ws, w.n, w.nrhs, e2e_step), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
            "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
@@ -487,9 +500,8 @@ def main():
         exact = prob.exact(oracle, pts, dens_np, tg)
         el = time.perf_counter() - t0
         got = out.cpu().numpy().astype(np.complex128 if not prob.stokes else np.float64)[..., tg]
-        what = "the Stokeslet sum" if prob.stokes else "Eq. (1)"
         res["cpu_baseline"] = {"value": m * w.nrhs / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-                               "sample": f"FP64 direct sum of {what} at {m} of the {w.n} targets ({el:.1f} s)"}
+                               "sample": f"FP64 direct sum of {prob.what()} at {m} of the {w.n} targets ({el:.1f} s)"}
         res["rel_err_vs_direct_sum"] = {"value": oracle.rel_l2(got, exact), "targets": m}
     print(json.dumps(res), flush=True)
     if pg:

@@ -158,6 +158,27 @@ ifgf_status ifgf_apply_stokes(ifgf_plan plan, const void* forces, int32_t nfield
 ifgf_status ifgf_apply_stokes_ex(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream,
                                  int32_t near, int64_t level_mask);
 
+/*
+ * Elasticity kernel: displacements of point forces in an infinite homogeneous isotropic elastic
+ * solid (Kelvin's solution of the Navier equations, one of the kernels Sec. 2 names),
+ *     u_i(x_l) = sum_{m != l} sum_j K_ij(x_l, x_m) f_j(x_m),
+ *     K_ij(x, y) = ((3 - 4 nu) delta_ij / r + (x_i - y_i)(x_j - y_j) / r^3) / (16 pi mu (1 - nu)),
+ * evaluated as ifgf_apply_stokes does (same centred factor, plan requirements, layouts,
+ * asynchrony and errors); at nu = 1/2 it is the Stokeslet divided by mu.
+ *
+ *   shear_modulus  mu, finite and > 0.
+ *   poisson_ratio  nu, in (-1, 1/2].
+ *
+ * Errors: as ifgf_apply_stokes, plus IFGF_ERR_INVALID_ARG for mu or nu out of range.
+ */
+ifgf_status ifgf_apply_elastic(ifgf_plan plan, const void* forces, int32_t nfield, void* displacement,
+                               double shear_modulus, double poisson_ratio, void* stream);
+
+/* ifgf_apply_elastic restricted to some contributions, as ifgf_apply_ex. */
+ifgf_status ifgf_apply_elastic_ex(ifgf_plan plan, const void* forces, int32_t nfield, void* displacement,
+                                  double shear_modulus, double poisson_ratio, void* stream, int32_t near,
+                                  int64_t level_mask);
+
 /* Release the plan and all its device memory to the library's pool (synchronous; see
  * ifgf_release_cached_memory).  NULL is accepted. */
 ifgf_status ifgf_plan_destroy(ifgf_plan plan);

@@ -87,6 +87,10 @@ def load(build: bool = True):
         lib.ifgf_apply_stokes.restype = ctypes.c_int
         lib.ifgf_apply_stokes_ex.argtypes = [vp, vp, i32, vp, vp, i32, i64]
         lib.ifgf_apply_stokes_ex.restype = ctypes.c_int
+        lib.ifgf_apply_elastic.argtypes = [vp, vp, i32, vp, dbl, dbl, vp]
+        lib.ifgf_apply_elastic.restype = ctypes.c_int
+        lib.ifgf_apply_elastic_ex.argtypes = [vp, vp, i32, vp, dbl, dbl, vp, i32, i64]
+        lib.ifgf_apply_elastic_ex.restype = ctypes.c_int
         lib.ifgf_plan_destroy.argtypes = [vp]
         lib.ifgf_plan_destroy.restype = ctypes.c_int
         lib.ifgf_plan_query.argtypes = [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
@@ -236,6 +240,21 @@ class Plan:
             _check(self._lib.ifgf_apply_stokes_ex(self._h, _ptr(forces), int(nfield), _ptr(velocity), _stream(stream),
                                                   1 if near else 0, int(level_mask)))
         return velocity
+
+    def apply_elastic(self, forces, displacement, shear_modulus: float, poisson_ratio: float,
+                      nfield: int | None = None, stream=None, near: bool = True, level_mask: int = -1):
+        """displacement <- Kelvin-solution sums of the force fields (kappa = 0 MIXED plans); forces and
+        displacement are [nfield][3][N] float32 in the caller's point order."""
+        if nfield is None:
+            nfield = 1 if len(forces.shape) == 2 else int(forces.shape[0])
+        if near and level_mask == -1:
+            _check(self._lib.ifgf_apply_elastic(self._h, _ptr(forces), int(nfield), _ptr(displacement),
+                                                float(shear_modulus), float(poisson_ratio), _stream(stream)))
+        else:
+            _check(self._lib.ifgf_apply_elastic_ex(self._h, _ptr(forces), int(nfield), _ptr(displacement),
+                                                   float(shear_modulus), float(poisson_ratio), _stream(stream),
+                                                   1 if near else 0, int(level_mask)))
+        return displacement
 
     def query(self, what: int, level: int = 0) -> np.ndarray:
         cnt = ctypes.c_int64(0)

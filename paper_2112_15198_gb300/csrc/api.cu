@@ -304,22 +304,25 @@ ifgf_status ifgf_apply(ifgf_plan plan, const void* densities, int32_t nrhs, void
     return ifgf_apply_ex(plan, densities, nrhs, out, stream, 1, -1);
 }
 
-ifgf_status ifgf_apply_stokes_ex(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream,
-                                 int32_t near, int64_t level_mask) {
-    if (!plan || !forces || !velocity) {
-        set_last_error("NULL plan, forces or velocity");
+namespace {
+
+// Shared checks and dispatch of the tensor-kernel applies (Stokeslet, Kelvin's solution).
+ifgf_status apply_tensor(ifgf_plan plan, const void* forces, int32_t nfield, void* out, void* stream, int32_t near,
+                         int64_t level_mask, const TensorKernel& tk, const char* name) {
+    if (!plan || !forces || !out) {
+        set_last_error("NULL plan, forces or output");
         return IFGF_ERR_INVALID_ARG;
     }
-    if (forces == velocity) {
-        set_last_error("velocity must not alias forces");
+    if (forces == out) {
+        set_last_error("the output must not alias the forces");
         return IFGF_ERR_INVALID_ARG;
     }
     if (plan->kappa != 0.0) {
-        set_last_error("the Stokes kernel needs a plan created with kappa = 0");
+        set_last_error(std::string("the ") + name + " kernel needs a plan created with kappa = 0");
         return IFGF_ERR_INVALID_ARG;
     }
     if (plan->precision != IFGF_PREC_MIXED) {
-        set_last_error("the Stokes kernel is built for IFGF_PREC_MIXED plans");
+        set_last_error(std::string("the ") + name + " kernel is built for IFGF_PREC_MIXED plans");
         return IFGF_ERR_UNSUPPORTED;
     }
     if (nfield < 1 || (3 * (int64_t)nfield + 1) / 2 > plan->max_nrhs) {
@@ -328,13 +331,39 @@ ifgf_status ifgf_apply_stokes_ex(ifgf_plan plan, const void* forces, int32_t nfi
     }
     return guard([&] {
         IFGF_CUDA(cudaSetDevice(plan->device));
-        apply_plan_stokes(*plan, static_cast<const float*>(forces), nfield, static_cast<float*>(velocity),
+        apply_plan_stokes(*plan, static_cast<const float*>(forces), nfield, static_cast<float*>(out), tk,
                           (cudaStream_t)stream, near != 0, level_mask);
     });
 }
 
+}  // namespace
+
+ifgf_status ifgf_apply_stokes_ex(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream,
+                                 int32_t near, int64_t level_mask) {
+    return apply_tensor(plan, forces, nfield, velocity, stream, near, level_mask, TensorKernel{}, "Stokes");
+}
+
 ifgf_status ifgf_apply_stokes(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream) {
     return ifgf_apply_stokes_ex(plan, forces, nfield, velocity, stream, 1, -1);
+}
+
+ifgf_status ifgf_apply_elastic_ex(ifgf_plan plan, const void* forces, int32_t nfield, void* displacement,
+                                  double shear_modulus, double poisson_ratio, void* stream, int32_t near,
+                                  int64_t level_mask) {
+    if (!(shear_modulus > 0.0) || !std::isfinite(shear_modulus) || !(poisson_ratio > -1.0) ||
+        !(poisson_ratio <= 0.5)) {
+        set_last_error("shear_modulus must be finite and > 0, poisson_ratio in (-1, 0.5]");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    TensorKernel tk;
+    tk.c = 1.0 / (16.0 * M_PI * shear_modulus * (1.0 - poisson_ratio));
+    tk.alpha = 3.0 - 4.0 * poisson_ratio;
+    return apply_tensor(plan, forces, nfield, displacement, stream, near, level_mask, tk, "elasticity");
+}
+
+ifgf_status ifgf_apply_elastic(ifgf_plan plan, const void* forces, int32_t nfield, void* displacement,
+                               double shear_modulus, double poisson_ratio, void* stream) {
+    return ifgf_apply_elastic_ex(plan, forces, nfield, displacement, shear_modulus, poisson_ratio, stream, 1, -1);
 }
 
 ifgf_status ifgf_plan_destroy(ifgf_plan plan) {

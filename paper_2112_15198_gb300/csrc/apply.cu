@@ -189,7 +189,7 @@ __device__ __forceinline__ T2 cheb_coeffs_smem(T2* f, T2* g, const R* __restrict
 
 // LevelDEvaluations with one block per leaf box: the box's sources (offset from the centre in
 // units of h, |u|^2 and the density) are staged in shared memory once and swept by every
-// (cone, node) of the box, up to 32 cones at a time. For the node x = x_k + (h/s) y (|y| = 1)
+// (cone, node) of the box, up to 32 cones at a time (8 for larger orders). For the node x = x_k + (h/s) y (|y| = 1)
 // and the source x' = x_k + h u, |x - x'|^2 / r^2 = q = 1 + s (s |u|^2 - 2 y.u), so
 //     g_k(x, x') = q^(-1/2) exp(i kappa h (s |u|^2 - 2 y.u) / (1 + q^(1/2))),
 // free of cancellation; then the coefficient transform of each cone by one warp.
@@ -204,9 +204,10 @@ k_leaf_box_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ cone
                int nrhs) {
     constexpr int P = PS * PT * PP;
     constexpr int NW = kLeafThreads / 32;
+    constexpr int NCP = P <= 75 ? kLeafCones : 8;  // cones per pass (shared memory below 48 KB)
     __shared__ float4 s_u[kLeafSrc];   // (u, |u|^2)
     __shared__ float2 s_a[kLeafSrc];
-    __shared__ float2 f[kLeafCones][P];
+    __shared__ float2 f[NCP][P];
     __shared__ float2 tmp[NW][P];
     const int b = blockIdx.x;
     const int r = blockIdx.y;
@@ -218,8 +219,8 @@ k_leaf_box_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ cone
     const float* Ws = W;
     const float* Wt = W + PS * PS;
     const float* Wp = Wt + PT * PT;
-    for (int cc = c0; cc < c1; cc += kLeafCones) {
-        const int ncc = min(kLeafCones, c1 - cc);
+    for (int cc = c0; cc < c1; cc += NCP) {
+        const int ncc = min(NCP, c1 - cc);
         const int items = ncc * P;
         for (int t0 = j0; t0 < j1; t0 += kLeafSrc) {
             const int nt = min(kLeafSrc, j1 - t0);
@@ -747,8 +748,10 @@ __global__ void k_prop_f64(const int32_t* __restrict__ pcone_box, const int32_t*
 // add I_P C_{k;gamma}(x) G(x, x_k).  Mixed variant: |x - x_k| = |c_A - c_k + d_A| with the
 // integer centre offset c_A - c_k = 2^(D-d+1) n, so
 //   kappa |x - x_k| = (kappa H_d sqrt(|n|^2) mod 2 pi) + kappa u (2 c.d_A + |d_A|^2)/(|x - x_k| + |c|).
-template <int PS, int PT, int PP>
-__global__ void __launch_bounds__(kThreads, 5) k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
+// NR value sets per thread (grid row y covers sets [NR y, NR y + NR)): the target's geometry, the
+// cone lookup and the centred factor are computed once for all of them.
+template <int PS, int PT, int PP, int NR>
+__global__ void __launch_bounds__(kThreads, NR == 1 ? 5 : 4) k_interp_f32(int64_t N, int sh, const int32_t* __restrict__ pbox_d, const int32_t* __restrict__ pbox_D,
                              const int4* __restrict__ kD, const int4* __restrict__ kd, const int32_t* __restrict__ ncs,
                              const int32_t* __restrict__ cs, const float4* __restrict__ off,
                              ConeMap cm, LevelGrid g, const float2* __restrict__ coef,
@@ -756,7 +759,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_interp_f32(int64_t N, int sh, c
                              int cstride, int nrhs, int* __restrict__ status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int r = blockIdx.y;
+    const int r0 = blockIdx.y * NR;
+    const int nv = min(NR, nrhs - r0);
     const int A = pbox_d[i];
     const int4 kl = kD[pbox_D[i]];
     const int4 kA = kd[A];
@@ -766,7 +770,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_interp_f32(int64_t N, int sh, c
     const float daz = (float)((2 * kl.z + 1) - ((2 * kA.z + 1) << sh)) + o.z;
     const float dd = fmaf(dax, dax, fmaf(day, day, daz * daz));
     const float cscale = (float)(2 << sh);
-    float2 acc = make_float2(0.f, 0.f);
+    float2 acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = make_float2(0.f, 0.f);
     const int nc = ncs[A];
     for (int t = 0; t < nc; ++t) {
         const int B = cs[(int64_t)A * kMaxCous + t];
@@ -780,7 +786,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_interp_f32(int64_t N, int sh, c
             set_status(status, IFGF_ERR_INTERNAL);
             continue;
         }
-        const float2 F = interp_f32<PS, PT, PP>(coef + ((int64_t)s * nrhs + r) * cstride, cl.ts, cl.tt, cl.tp);
         const int nx = kA.x - kb.x, ny = kA.y - kb.y, nz = kA.z - kb.z;
         const int nn = nx * nx + ny * ny + nz * nz;
         const float cx = cscale * nx, cy = cscale * ny, cz = cscale * nz;
@@ -789,13 +794,26 @@ __global__ void __launch_bounds__(kThreads, 5) k_interp_f32(int64_t N, int sh, c
         const float corr = __fdividef(num, cl.r + cn);
         const float2 e = cis_f32(fmaf(ku, corr, __ldg(&phtab[nn])));
         const float w = __fdividef(inv4piu, cl.r);
-        const float2 tv = cmul(F, make_float2(e.x * w, e.y * w));
-        acc.x += tv.x;
-        acc.y += tv.y;
+        const float2 ew = make_float2(e.x * w, e.y * w);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (r < nv) {
+                const float2 F =
+                    interp_f32<PS, PT, PP>(coef + ((int64_t)s * nrhs + r0 + r) * cstride, cl.ts, cl.tt, cl.tp);
+                const float2 tv = cmul(F, ew);
+                acc[r].x += tv.x;
+                acc[r].y += tv.y;
+            }
+        }
     }
-    float2* dst = Is + (int64_t)r * N + i;
-    const float2 prev = *dst;
-    *dst = make_float2(prev.x + acc.x, prev.y + acc.y);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        if (r < nv) {
+            float2* dst = Is + (int64_t)(r0 + r) * N + i;
+            const float2 prev = *dst;
+            *dst = make_float2(prev.x + acc[r].x, prev.y + acc[r].y);
+        }
+    }
 }
 
 template <int PS, int PT, int PP>
@@ -1269,7 +1287,6 @@ __global__ void k_leaf_f32_multi(const int32_t* __restrict__ cone_box, const int
                                  const float2* __restrict__ as, int64_t N, float kh, float hinv,
                                  const float* __restrict__ W, float2* __restrict__ coef, int cstride, int nrhs) {
     constexpr int P = PS * PT * PP;
-    constexpr int BT = ((P + 31) / 32) * 32;
     __shared__ float2 f[NR][P], tmp[NR][P];
     const int cone = blockIdx.x;
     const int rhs0 = blockIdx.y * NR;
@@ -1312,12 +1329,15 @@ __global__ void k_leaf_f32_multi(const int32_t* __restrict__ cone_box, const int
                                       nrhs - rhs0);
 }
 
-// ---- Stokes kernel ------------------------------------------------------------------------
-// The Stokeslet at unit viscosity, S_ij(x,y) = (delta_ij/r + r_i r_j/r^3)/(8 pi) with r = x - y,
-// acting on real force vectors (the Stokes equations are among the kernels Sec. 2 names for
-// Eq. (1)). Its centred factor is the Laplace one, G_0(x,x_k) = 1/(4 pi |x - x_k|), and its
-// analytic factor S(x,x')/G_0(x,x_k) (Eq. (3)) is smooth in the cone variables, so that each
-// velocity component is carried through propagation and interpolation as a kappa = 0 value set.
+// ---- Stokes and elasticity kernels ----------------------------------------------------------
+// Green tensors of the form S_ij(x,y) = c (alpha delta_ij/r + r_i r_j/r^3) with r = x - y, acting
+// on real force vectors (the Stokes and elasticity equations are among the kernels Sec. 2 names
+// for Eq. (1)): the Stokeslet (c = 1/(8 pi mu), alpha = 1) and Kelvin's solution of linear
+// elasticity (c = 1/(16 pi mu (1 - nu)), alpha = 3 - 4 nu). Their centred factor is the Laplace
+// one, G_0(x,x_k) = 1/(4 pi |x - x_k|), and their analytic factor S(x,x')/G_0(x,x_k) (Eq. (3))
+// is smooth in the cone variables, so that each velocity (displacement) component is carried
+// through propagation and interpolation as a kappa = 0 value set. The kernels stage alpha f and
+// use beta = 1/alpha: S f = c (alpha f + r (r . alpha f) beta / r^2) / |r|.
 // The three real components of force field f occupy reals q = 3f + c of the complex slots, slot
 // q/2, real part for even q: ceil(3 nf / 2) complex sets. Forces in Morton order are SoA,
 // fs[(3 f + c) N + j]; the kernels below take fields in pairs starting at an even field (three
@@ -1330,7 +1350,7 @@ template <int NF>
 __global__ void __launch_bounds__(kNearThreads)
 k_near_stokes_f32(const int4* __restrict__ kD, const int32_t* __restrict__ startD, const int32_t* __restrict__ nnb,
                   const int32_t* __restrict__ nb, const float4* __restrict__ off, const float* __restrict__ fs,
-                  float2* __restrict__ Is, int64_t N, float inv8piu, int f0) {
+                  float2* __restrict__ Is, int64_t N, float alpha, float beta, float cu, int f0) {
     __shared__ float4 s_p[kNearTile];  // source position in the target box's grid frame; w = source index
     __shared__ float4 s_f[NF][kNearTile];
     const int l = blockIdx.x;
@@ -1366,7 +1386,7 @@ k_near_stokes_f32(const int4* __restrict__ kD, const int32_t* __restrict__ start
 #pragma unroll
                     for (int r = 0; r < NF; ++r) {
                         const float* fr = fs + (int64_t)3 * (f + r) * N + j;
-                        s_f[r][tid] = make_float4(__ldg(fr), __ldg(fr + N), __ldg(fr + 2 * N), 0.f);
+                        s_f[r][tid] = make_float4(alpha * __ldg(fr), alpha * __ldg(fr + N), alpha * __ldg(fr + 2 * N), 0.f);
                     }
                 }
                 __syncthreads();
@@ -1377,11 +1397,10 @@ k_near_stokes_f32(const int4* __restrict__ kD, const int32_t* __restrict__ start
                         const float vx = oi.x - pj.x, vy = oi.y - pj.y, vz = oi.z - pj.z;
                         const float r2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
                         const float rinv = rsqrtf(r2);
-                        const float rinv2 = rinv * rinv;
+                        const float rinv2 = rinv * rinv * beta;
 #pragma unroll
                         for (int r = 0; r < NF; ++r) {
-                            const float4 fj = s_f[r][k];
-                            // S f = (f + r (r . f) / r^2) / (8 pi |r|)
+                            const float4 fj = s_f[r][k];  // alpha f
                             const float t = fmaf(vx, fj.x, fmaf(vy, fj.y, vz * fj.z)) * rinv2;
                             acc[r][0] = fmaf(rinv, fmaf(t, vx, fj.x), acc[r][0]);
                             acc[r][1] = fmaf(rinv, fmaf(t, vy, fj.y), acc[r][1]);
@@ -1399,69 +1418,158 @@ k_near_stokes_f32(const int4* __restrict__ kD, const int32_t* __restrict__ start
         }
         if (active && part == 0) {
             float2* o = Is + (int64_t)(3 * f / 2) * N + i;
-            o[0] = make_float2(acc[0][0] * inv8piu, acc[0][1] * inv8piu);
+            o[0] = make_float2(acc[0][0] * cu, acc[0][1] * cu);
             if constexpr (NF == 2) {
-                o[N] = make_float2(acc[0][2] * inv8piu, acc[1][0] * inv8piu);
-                o[2 * N] = make_float2(acc[1][1] * inv8piu, acc[1][2] * inv8piu);
+                o[N] = make_float2(acc[0][2] * cu, acc[1][0] * cu);
+                o[2 * N] = make_float2(acc[1][1] * cu, acc[1][2] * cu);
             } else {
-                o[N] = make_float2(acc[0][2] * inv8piu, 0.f);
+                o[N] = make_float2(acc[0][2] * cu, 0.f);
             }
         }
     }
 }
 
-// Leaf level (Algorithm 6) for the Stokeslet: at node y of leaf cone (k, gamma) the analytic
-// factor is S(y, x')/G_0(y, x_k) = (rq/2)(I + w w^T rq^2), w = y_hat - s u (u = (x' - x_k)/h,
-// rq = 1/|w|), then the coefficient transform of the block's complex slots.
+// Leaf level (Algorithm 6) for these kernels, one block per leaf box as in k_leaf_box_f32: the box's
+// sources (u = (x' - x_k)/h and the NF force vectors) are staged in shared memory once per pass and
+// swept by every (cone, node) of the box, NCP cones at a time. At node y = x_k + (h/s) yhat the
+// analytic factor is S(y, x')/G_0(y, x_k) = 4 pi c rq (alpha I + w w^T rq^2) with w = yhat - s u
+// and rq = 1/|w|; the factor 4 pi c (fscale) is applied to the coefficients. Then one warp per
+// (cone, complex set) computes the coefficients.
 template <int PS, int PT, int PP, int NF>
-__global__ void k_leaf_stokes_f32(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam,
-                                  LevelGrid g, const int32_t* __restrict__ startD, const float4* __restrict__ off,
-                                  const float* __restrict__ fs, int64_t N, float hinv, const float* __restrict__ W,
-                                  float2* __restrict__ coef, int cstride, int nrhs, int f0) {
+__global__ void __launch_bounds__(kLeafThreads)
+k_leaf_stokes_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ cone_gam, LevelGrid g,
+                  const int32_t* __restrict__ startD, const float4* __restrict__ off, const float* __restrict__ fs,
+                  int64_t N, float hinv, const float* __restrict__ W, float2* __restrict__ coef, int cstride,
+                  int nrhs, float alpha, float beta, float fscale, int f0) {
     constexpr int P = PS * PT * PP;
-    constexpr int NS = NF == 2 ? 3 : 2;  // complex slots of the block's fields
-    __shared__ float2 v[NS][P], tmp[NS][P];
-    const int cone = blockIdx.x;
+    constexpr int NS = NF == 2 ? 3 : 2;  // complex sets of the block's fields
+    constexpr int NW = kLeafThreads / 32;
+    constexpr int NCP = P <= 75 ? 16 : 2;  // cones per pass (shared memory below 48 KB)
+    __shared__ float4 s_u[kLeafSrc];
+    __shared__ float4 s_f[NF][kLeafSrc];
+    __shared__ float2 v[NCP][NS][P];
+    __shared__ float2 tmp[NW][P];
+    const int b = blockIdx.x;
     const int f = f0 + NF * blockIdx.y;
-    const int n = threadIdx.x;
-    const int b = cone_box[cone];
-    if (n < P) {
-        const int gam = cone_gam[cone];
-        const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
-        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
-        const float s = g.snode[is * PS + ia];
-        const float st = g.stn[it * PT + ib], ct = g.ctn[it * PT + ib];
-        const float yx = st * g.cpn[ip * PP + ic], yy = st * g.spn[ip * PP + ic], yz = ct;
-        float acc[NF][3];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c0 = bcs[b], c1 = bcs[b + 1];
+    if (c0 == c1) return;
+    const int j0 = startD[b], j1 = startD[b + 1];
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    for (int cc = c0; cc < c1; cc += NCP) {
+        const int ncc = min(NCP, c1 - cc);
+        const int items = ncc * P;
+        for (int t0 = j0; t0 < j1; t0 += kLeafSrc) {
+            const int nt = min(kLeafSrc, j1 - t0);
+            __syncthreads();
+            if (tid < nt) {
+                const int j = t0 + tid;
+                const float4 o = __ldg(&off[j]);
+                s_u[tid] = make_float4(o.x * hinv, o.y * hinv, o.z * hinv, 0.f);
 #pragma unroll
-        for (int r = 0; r < NF; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.f;
-        for (int j = startD[b]; j < startD[b + 1]; ++j) {
-            const float4 o = __ldg(&off[j]);
-            const float ux = o.x * hinv, uy = o.y * hinv, uz = o.z * hinv;
-            const float wx = fmaf(-s, ux, yx), wy = fmaf(-s, uy, yy), wz = fmaf(-s, uz, yz);
-            const float q = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
-            const float rq = rsqrtf(q);
-            const float rq2 = rq * rq;
+                for (int r = 0; r < NF; ++r) {
+                    const float* fr = fs + (int64_t)3 * (f + r) * N + j;
+                    s_f[r][tid] = make_float4(alpha * __ldg(fr), alpha * __ldg(fr + N), alpha * __ldg(fr + 2 * N), 0.f);
+                }
+            }
+            __syncthreads();
+            for (int item = tid; item < items; item += kLeafThreads) {
+                const int cl = item / P, n = item - (item / P) * P;
+                const int gam = __ldg(&cone_gam[cc + cl]);
+                const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
+                const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+                const float sn = __ldg(&g.snode[is * PS + ia]);
+                const float st = __ldg(&g.stn[it * PT + ib]), ct = __ldg(&g.ctn[it * PT + ib]);
+                const float yx = st * __ldg(&g.cpn[ip * PP + ic]), yy = st * __ldg(&g.spn[ip * PP + ic]), yz = ct;
+                float acc[NF][3];
+                if (t0 == j0) {
 #pragma unroll
-            for (int r = 0; r < NF; ++r) {
-                const float* fr = fs + (int64_t)3 * (f + r) * N + j;
-                const float fx = __ldg(fr), fy = __ldg(fr + N), fz = __ldg(fr + 2 * N);
-                const float t = fmaf(wx, fx, fmaf(wy, fy, wz * fz)) * rq2;
-                acc[r][0] = fmaf(rq, fmaf(t, wx, fx), acc[r][0]);
-                acc[r][1] = fmaf(rq, fmaf(t, wy, fy), acc[r][1]);
-                acc[r][2] = fmaf(rq, fmaf(t, wz, fz), acc[r][2]);
+                    for (int r = 0; r < NF; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.f;
+                } else {
+                    const float2 a0 = v[cl][0][n], a1 = v[cl][1][n];
+                    acc[0][0] = a0.x;
+                    acc[0][1] = a0.y;
+                    acc[0][2] = a1.x;
+                    if constexpr (NF == 2) {
+                        const float2 a2 = v[cl][2][n];
+                        acc[1][0] = a1.y;
+                        acc[1][1] = a2.x;
+                        acc[1][2] = a2.y;
+                    }
+                }
+#pragma unroll 2
+                for (int j = 0; j < nt; ++j) {
+                    const float4 u = s_u[j];
+                    const float wx = fmaf(-sn, u.x, yx), wy = fmaf(-sn, u.y, yy), wz = fmaf(-sn, u.z, yz);
+                    const float q = fmaf(wx, wx, fmaf(wy, wy, wz * wz));
+                    const float rq = rsqrtf(q);
+                    const float rq2 = rq * rq * beta;
+#pragma unroll
+                    for (int r = 0; r < NF; ++r) {
+                        const float4 fj = s_f[r][j];  // alpha f
+                        const float t = fmaf(wx, fj.x, fmaf(wy, fj.y, wz * fj.z)) * rq2;
+                        acc[r][0] = fmaf(rq, fmaf(t, wx, fj.x), acc[r][0]);
+                        acc[r][1] = fmaf(rq, fmaf(t, wy, fj.y), acc[r][1]);
+                        acc[r][2] = fmaf(rq, fmaf(t, wz, fj.z), acc[r][2]);
+                    }
+                }
+                v[cl][0][n] = make_float2(acc[0][0], acc[0][1]);
+                if constexpr (NF == 2) {
+                    v[cl][1][n] = make_float2(acc[0][2], acc[1][0]);
+                    v[cl][2][n] = make_float2(acc[1][1], acc[1][2]);
+                } else {
+                    v[cl][1][n] = make_float2(acc[0][2], 0.f);
+                }
             }
         }
-        v[0][n] = make_float2(0.5f * acc[0][0], 0.5f * acc[0][1]);
-        if constexpr (NF == 2) {
-            v[1][n] = make_float2(0.5f * acc[0][2], 0.5f * acc[1][0]);
-            v[2][n] = make_float2(0.5f * acc[1][1], 0.5f * acc[1][2]);
-        } else {
-            v[1][n] = make_float2(0.5f * acc[0][2], 0.f);
+        __syncthreads();
+        for (int x = warp; x < ncc * NS; x += NW) {  // coefficient transform, one warp per (cone, set)
+            const int cl = x / NS, sl = x - (x / NS) * NS;
+            float2* fv = v[cl][sl];
+            float2* tv = tmp[warp];
+            for (int n = lane; n < P; n += 32) {
+                const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < PP; ++k) {
+                    const float w = Wp[qc * PP + k];
+                    const float2 z = fv[(qa * PT + qb) * PP + k];
+                    a.x = fmaf(w, z.x, a.x);
+                    a.y = fmaf(w, z.y, a.y);
+                }
+                tv[n] = a;
+            }
+            __syncwarp();
+            for (int n = lane; n < P; n += 32) {
+                const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < PT; ++k) {
+                    const float w = Wt[qb * PT + k];
+                    const float2 z = tv[(qa * PT + k) * PP + qc];
+                    a.x = fmaf(w, z.x, a.x);
+                    a.y = fmaf(w, z.y, a.y);
+                }
+                fv[n] = a;
+            }
+            __syncwarp();
+            for (int n = lane; n < P; n += 32) {
+                const int qc = n % PP, qb = (n / PP) % PT, qa = n / (PP * PT);
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < PS; ++k) {
+                    const float w = Ws[qa * PS + k];
+                    const float2 z = fv[(k * PT + qb) * PP + qc];
+                    a.x = fmaf(w, z.x, a.x);
+                    a.y = fmaf(w, z.y, a.y);
+                }
+                coef[((int64_t)(cc + cl) * nrhs + 3 * f / 2 + sl) * cstride + n] = make_float2(fscale * a.x, fscale * a.y);
+            }
+            __syncwarp();
         }
     }
-    __syncthreads();
-    cone_coeffs_block<PS, PT, PP, NS>(v, tmp, W, coef + ((int64_t)cone * nrhs + 3 * f / 2) * cstride, cstride, NS);
 }
 
 // Velocities back to the caller's order: real q of the slots -> out[q][perm[i]].
@@ -1491,27 +1599,46 @@ void for_each_slice(const Plan& p, int d, F&& launch) {
     }
 }
 
+// Interpolation to the targets of level d for nrhs value sets: one set per thread for a single
+// set, else two or four sets per thread sharing the geometry.
+template <int PS, int PT, int PP>
+void launch_interp_f32(Plan& p, int d, int nrhs, float2* Is, cudaStream_t s) {
+    const int64_t N = p.N;
+    Level& L = p.L[d];
+    Level& LD = p.L[p.D];
+    const int sh = p.D - d;
+    const float ku = (float)(p.kappa * p.u);
+    const float inv4piu = (float)(1.0 / (4.0 * M_PI * p.u));
+    const float2* c = (const float2*)level_coef(p, d, nrhs);
+    const unsigned gx = grid_for(N, kThreads);
+    if (nrhs == 1)
+        IFGF_LAUNCH((k_interp_f32<PS, PT, PP, 1>), dim3(gx, 1), kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k,
+                    L.ncs, L.cs, p.off, L.cmap(), L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status);
+    else if (nrhs <= 3)
+        IFGF_LAUNCH((k_interp_f32<PS, PT, PP, 2>), dim3(gx, (nrhs + 1) / 2), kThreads, 0, s, N, sh, L.pbox, LD.pbox,
+                    LD.k, L.k, L.ncs, L.cs, p.off, L.cmap(), L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs,
+                    p.d_status);
+    else
+        IFGF_LAUNCH((k_interp_f32<PS, PT, PP, 4>), dim3(gx, (nrhs + 3) / 4), kThreads, 0, s, N, sh, L.pbox, LD.pbox,
+                    LD.k, L.k, L.ncs, L.cs, p.off, L.cmap(), L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs,
+                    p.d_status);
+}
+
 // Levels D..3 of the many-density path: interpolation to the targets of level d (Algorithm 8),
 // then propagation into level d-1 (Algorithm 7) on the tensor cores.
 template <int NT, int PS, int PT, int PP>
 void sweep_levels_mma(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mask) {
     constexpr int P = PS * PT * PP;
     constexpr int NR = 4 * NT;
-    const int64_t N = p.N;
     const int D = p.D;
-    Level& LD = p.L[D];
     const float ku = (float)(p.kappa * p.u);
-    const float inv4piu = (float)(1.0 / (4.0 * M_PI * p.u));
-    const dim3 gN(grid_for(N, kThreads), nrhs);
     const unsigned rb = (unsigned)((nrhs + NR - 1) / NR);
     for (int d = D; d >= 3; --d) {
         Level& L = p.L[d];
         const int sh = D - d;
         if ((mask >> d) & 1) {
             TimedScope ts_(TK_INTERP, s);
-            IFGF_LAUNCH((k_interp_f32<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs, L.cs,
-                        p.off, L.cmap(), L.g, (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu, Is,
-                        p.cstride, nrhs, p.d_status);
+            launch_interp_f32<PS, PT, PP>(p, d, nrhs, Is, s);
         }
         if (d == 3) break;
         Level& Lp = p.L[d - 1];
@@ -1594,20 +1721,14 @@ void run_apply_multi(Plan& p, const void* dens, int nrhs, void* out, cudaStream_
 // level has them.
 template <int PS, int PT, int PP>
 void sweep_levels_f32(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mask) {
-    const int64_t N = p.N;
     const int D = p.D;
-    Level& LD = p.L[D];
     const float ku = (float)(p.kappa * p.u);
-    const float inv4piu = (float)(1.0 / (4.0 * M_PI * p.u));
-    const dim3 gN(grid_for(N, kThreads), nrhs);
     for (int d = D; d >= 3; --d) {
         Level& L = p.L[d];
         const int sh = D - d;
         if ((mask >> d) & 1) {
             TimedScope ts_(TK_INTERP, s);
-            IFGF_LAUNCH((k_interp_f32<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs, L.cs,
-                        p.off, L.cmap(), L.g, (const float2*)level_coef(p, d, nrhs), L.phtab, ku, inv4piu, Is,
-                        p.cstride, nrhs, p.d_status);
+            launch_interp_f32<PS, PT, PP>(p, d, nrhs, Is, s);
         }
         if (d == 3) break;
         Level& Lp = p.L[d - 1];
@@ -1748,20 +1869,20 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
     }
 }
 
-// Stokes apply of nf force fields ([nf][3][N] float, caller's order) into velocities of the
-// same layout: Stokes near field and leaf level, then the kappa = 0 level sweep on the
-// ceil(3 nf / 2) complex slots.
+// Apply of S = c (alpha I/r + r r^T/r^3) to nf force fields ([nf][3][N] float, caller's order)
+// into velocities (displacements) of the same layout: near field and leaf level of this kernel,
+// then the kappa = 0 level sweep on the ceil(3 nf / 2) complex slots.
 template <int PS, int PT, int PP>
-void run_apply_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStream_t s, bool near, int64_t mask) {
-    constexpr int P = PS * PT * PP;
-    constexpr int BT = ((P + 31) / 32) * 32;
+void run_apply_stokes(Plan& p, const float* forces, int nf, float* vel, const TensorKernel& tk, cudaStream_t s,
+                      bool near, int64_t mask) {
     const int64_t N = p.N;
     const int D = p.D;
     Level& LD = p.L[D];
     const int nreal = 3 * nf, slots = (nreal + 1) / 2, pairs = nf / 2;
     float* fs = (float*)p.a_s;
     float2* Is = (float2*)p.I_s;
-    const float inv8piu = (float)(1.0 / (8.0 * M_PI * p.u));
+    const float alpha = (float)tk.alpha, beta = (float)(1.0 / tk.alpha);
+    const float cu = (float)(tk.c / p.u), fscale = (float)(4.0 * M_PI * tk.c);
     const dim3 gR(grid_for(N, kThreads), nreal);
     {
         TimedScope ts_(TK_PERM, s);
@@ -1771,10 +1892,10 @@ void run_apply_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStre
         TimedScope ts_(TK_NEAR, s);
         if (pairs > 0)
             IFGF_LAUNCH(k_near_stokes_f32<2>, dim3((unsigned)LD.n, pairs), kNearThreads, 0, s, LD.k, LD.start, LD.nnb,
-                        LD.nb, p.off, fs, Is, N, inv8piu, 0);
+                        LD.nb, p.off, fs, Is, N, alpha, beta, cu, 0);
         if (nf & 1)
             IFGF_LAUNCH(k_near_stokes_f32<1>, dim3((unsigned)LD.n, 1), kNearThreads, 0, s, LD.k, LD.start, LD.nnb,
-                        LD.nb, p.off, fs, Is, N, inv8piu, nf - 1);
+                        LD.nb, p.off, fs, Is, N, alpha, beta, cu, nf - 1);
     } else {
         IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * slots, s));
     }
@@ -1783,11 +1904,13 @@ void run_apply_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStre
         float2* cD = (float2*)level_coef(p, D, slots);
         const float hinv = 1.0f / LD.g.hg;
         if (pairs > 0)
-            IFGF_LAUNCH((k_leaf_stokes_f32<PS, PT, PP, 2>), dim3((unsigned)LD.nc, pairs), BT, 0, s, LD.cone_box,
-                        LD.cone_gam, LD.g, LD.start, p.off, fs, N, hinv, p.Wf, cD, p.cstride, slots, 0);
+            IFGF_LAUNCH((k_leaf_stokes_f32<PS, PT, PP, 2>), dim3((unsigned)LD.n, pairs), kLeafThreads, 0, s, LD.bcs,
+                        LD.cone_gam, LD.g, LD.start, p.off, fs, N, hinv, p.Wf, cD, p.cstride, slots, alpha, beta,
+                        fscale, 0);
         if (nf & 1)
-            IFGF_LAUNCH((k_leaf_stokes_f32<PS, PT, PP, 1>), dim3((unsigned)LD.nc, 1), BT, 0, s, LD.cone_box,
-                        LD.cone_gam, LD.g, LD.start, p.off, fs, N, hinv, p.Wf, cD, p.cstride, slots, nf - 1);
+            IFGF_LAUNCH((k_leaf_stokes_f32<PS, PT, PP, 1>), dim3((unsigned)LD.n, 1), kLeafThreads, 0, s, LD.bcs,
+                        LD.cone_gam, LD.g, LD.start, p.off, fs, N, hinv, p.Wf, cD, p.cstride, slots, alpha, beta,
+                        fscale, nf - 1);
     }
     sweep_levels_mixed<PS, PT, PP>(p, slots, Is, s, mask);
     {
@@ -1814,7 +1937,8 @@ void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, 
     }
 }
 
-void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStream_t s, bool near, int64_t mask) {
+void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, const TensorKernel& tk, cudaStream_t s,
+                       bool near, int64_t mask) {
     // force fields in blocks whose ceil(3 nfb / 2) slots fit the arena's rhs_block value sets;
     // an even block size keeps every block but the last free of a half-empty slot
     int nfb = std::min(2 * p.rhs_block / 3, 21844);  // 3 nfb real sets fit a grid's y extent
@@ -1825,9 +1949,9 @@ void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStr
         const float* f = forces + (size_t)3 * f0 * p.N;
         float* u = vel + (size_t)3 * f0 * p.N;
         if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
-            run_apply_stokes<3, 5, 5>(p, f, nb, u, s, near, mask);
+            run_apply_stokes<3, 5, 5>(p, f, nb, u, tk, s, near, mask);
         else if (p.Ps == 5 && p.Pt == 7 && p.Pp == 7)
-            run_apply_stokes<5, 7, 7>(p, f, nb, u, s, near, mask);
+            run_apply_stokes<5, 7, 7>(p, f, nb, u, tk, s, near, mask);
         else
             fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
     }

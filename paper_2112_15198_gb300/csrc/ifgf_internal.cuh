@@ -262,7 +262,14 @@ inline char* level_coef(const Plan& p, int d, int nb) {
 }
 void destroy_plan(Plan& p);
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask);
-void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, cudaStream_t s, bool near, int64_t mask);
+// Green tensor c (alpha delta_ij / r + r_i r_j / r^3): the Stokeslet (c = 1/(8 pi mu), alpha = 1)
+// or Kelvin's solution of linear elasticity (c = 1/(16 pi mu (1 - nu)), alpha = 3 - 4 nu).
+struct TensorKernel {
+    double c = 0.039788735772973836;  // 1/(8 pi)
+    double alpha = 1.0;
+};
+void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, const TensorKernel& tk, cudaStream_t s,
+                       bool near, int64_t mask);
 
 // =========================================================================================
 // Device helpers

@@ -171,6 +171,19 @@ def test_higher_orders_fp64():
     assert oracle.rel_l2(_apply(gp, dens, "fp64"), exact) < 2e-6
 
 
+def test_higher_orders_mixed():
+    """Orders (5,7,7) on the mixed path (generic propagation, leaf in passes of 8 cones)."""
+    pts = W.fibonacci_sphere(3000)
+    kappa = 2 * math.pi * 2
+    dens = W.densities(3000, 2, 8)
+    op = oracle.Plan(pts, kappa, orders=(5, 7, 7), levels=4)
+    gp = _plan(pts, kappa, precision="mixed", orders=(5, 7, 7), levels=4, max_nrhs=2)
+    got = _apply(gp, dens, "mixed")
+    ref = op.apply(dens)
+    for r in range(2):
+        assert oracle.rel_l2(got[r], ref[r]) < 3e-5
+
+
 @pytest.mark.parametrize("what", ["duplicate", "nan", "n1", "kappa", "levels", "orders", "host_points"])
 def test_invalid_input_rejected(what):
     pts = W.random_cloud(100, seed=1)

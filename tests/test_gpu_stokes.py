@@ -142,3 +142,65 @@ def test_stokes_invalid_arguments():
     ok = _plan(pts, 1)
     with pytest.raises(ifgf.IFGFError):
         ok.apply_stokes(F, F)
+
+
+# ---- elasticity (Kelvin's solution), the same kernels with alpha = 3 - 4 nu ------------------
+
+def _elastic(plan, f, mu, nu, **kw):
+    F = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)).to(DEV)
+    U = torch.empty_like(F)
+    plan.apply_elastic(F, U, mu, nu, **kw)
+    torch.cuda.synchronize()
+    return U.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("nf", [1, 3])
+@pytest.mark.parametrize("nu", [0.0, 0.3, 0.45])
+def test_elastic_matches_cpu_ifgf(nf, nu):
+    pts = W.fibonacci_sphere(12288)
+    f = _forces(nf, pts.shape[1], 60 + nf)
+    ref = oracle.Plan(pts, 0.0).apply_elastic(f, 1.7, nu)
+    gp = _plan(pts, nf)
+    _check_fields(_elastic(gp, f, 1.7, nu), ref, 3e-5)
+    assert gp.status() == 0
+
+
+def test_elastic_at_half_is_stokes_over_mu():
+    """nu = 1/2: Kelvin's solution is the Stokeslet over mu; with mu = 2 every scale factor halves
+    exactly, so the result is bit for bit half the Stokes result."""
+    pts = W.fibonacci_sphere(12288)
+    f = _forces(2, pts.shape[1], 5)
+    gp = _plan(pts, 2)
+    assert np.array_equal(_elastic(gp, f, 2.0, 0.5), 0.5 * _stokes(gp, f))
+
+
+def test_elastic_vs_direct_sum_sampled():
+    pts = W.fibonacci_sphere(393216)
+    f = _forces(1, pts.shape[1], 32)
+    tgt = W.targets(pts.shape[1], 100, 232)
+    exact = oracle.elastic_direct_sum(pts, f, 1.7, 0.3, tgt)
+    got = _elastic(_plan(pts, 1), f, 1.7, 0.3)[:, :, tgt]
+    err = oracle.rel_l2(got, exact)
+    print(f"sphere32 points, elasticity: rel. L2 error on {len(tgt)} targets = {err:.3e}")
+    assert err < 5e-4
+
+
+def test_elastic_invalid_parameters():
+    pts = W.fibonacci_sphere(2048)
+    F = torch.zeros((1, 3, 2048), dtype=torch.float32, device=DEV)
+    U = torch.empty_like(F)
+    gp = _plan(pts, 1)
+    for mu, nu in ((0.0, 0.3), (-1.0, 0.3), (1.0, 0.6), (1.0, -1.0), (float("inf"), 0.3)):
+        with pytest.raises(ifgf.IFGFError) as e:
+            gp.apply_elastic(F, U, mu, nu)
+        assert e.value.status == 1
+
+
+# ---- higher orders on the mixed path -------------------------------------------------------
+
+def test_stokes_higher_orders():
+    pts = W.fibonacci_sphere(3000)
+    f = _forces(1, pts.shape[1], 9)
+    ref = oracle.Plan(pts, 0.0, orders=(5, 7, 7), levels=4).apply_stokes(f)
+    gp = _plan(pts, 1, orders=(5, 7, 7), levels=4)
+    _check_fields(_stokes(gp, f), ref, 3e-5)
