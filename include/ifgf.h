@@ -141,16 +141,15 @@ ifgf_status ifgf_apply_ex(ifgf_plan plan, const void* densities, int32_t nrhs, v
  * and the analytic factor of Eq. (3) is S(x, x') divided by it.  Asynchronous on `stream`, like
  * ifgf_apply.
  *
- *   plan      created with kappa = 0 and precision IFGF_PREC_MIXED, and with
- *             opt.max_nrhs >= ceil(3 nfield / 2) (the three velocity components of a field are
- *             carried as real and imaginary parts of complex value sets, two per set).
- *   forces    device, [nfield][3][N] float32 (component-major per field), the caller's point
- *             order.  Read only.
+ *   plan      created with kappa = 0 and opt.max_nrhs >= ceil(3 nfield / 2) (the three velocity
+ *             components of a field are carried as real and imaginary parts of complex value
+ *             sets, two per set).
+ *   forces    device, [nfield][3][N] float32 (MIXED plan) or float64 (FP64 plan), component-major
+ *             per field, the caller's point order.  Read only.
  *   nfield    number of force fields, >= 1.
  *   velocity  device, same layout and type as forces; overwritten.  Must not alias it.
  *
- * Errors: IFGF_ERR_INVALID_ARG for NULL pointers, aliasing, kappa != 0 or nfield out of range;
- * IFGF_ERR_UNSUPPORTED for an FP64 plan.
+ * Errors: IFGF_ERR_INVALID_ARG for NULL pointers, aliasing, kappa != 0 or nfield out of range.
  */
 ifgf_status ifgf_apply_stokes(ifgf_plan plan, const void* forces, int32_t nfield, void* velocity, void* stream);
 

@@ -230,8 +230,8 @@ class Plan:
 
     def apply_stokes(self, forces, velocity, nfield: int | None = None, stream=None, near: bool = True,
                      level_mask: int = -1):
-        """velocity <- Stokeslet sums of the force fields (kappa = 0 MIXED plans); forces/velocity are
-        [nfield][3][N] float32 in the caller's point order."""
+        """velocity <- Stokeslet sums of the force fields (kappa = 0 plans); forces/velocity are
+        [nfield][3][N] float32 (mixed plans) or float64 (fp64 plans) in the caller's point order."""
         if nfield is None:
             nfield = 1 if len(forces.shape) == 2 else int(forces.shape[0])
         if near and level_mask == -1:
@@ -243,8 +243,8 @@ class Plan:
 
     def apply_elastic(self, forces, displacement, shear_modulus: float, poisson_ratio: float,
                       nfield: int | None = None, stream=None, near: bool = True, level_mask: int = -1):
-        """displacement <- Kelvin-solution sums of the force fields (kappa = 0 MIXED plans); forces and
-        displacement are [nfield][3][N] float32 in the caller's point order."""
+        """displacement <- Kelvin-solution sums of the force fields (kappa = 0 plans); forces and
+        displacement are [nfield][3][N] float32 (mixed) or float64 (fp64) in the caller's point order."""
         if nfield is None:
             nfield = 1 if len(forces.shape) == 2 else int(forces.shape[0])
         if near and level_mask == -1:

@@ -321,18 +321,13 @@ ifgf_status apply_tensor(ifgf_plan plan, const void* forces, int32_t nfield, voi
         set_last_error(std::string("the ") + name + " kernel needs a plan created with kappa = 0");
         return IFGF_ERR_INVALID_ARG;
     }
-    if (plan->precision != IFGF_PREC_MIXED) {
-        set_last_error(std::string("the ") + name + " kernel is built for IFGF_PREC_MIXED plans");
-        return IFGF_ERR_UNSUPPORTED;
-    }
     if (nfield < 1 || (3 * (int64_t)nfield + 1) / 2 > plan->max_nrhs) {
         set_last_error("nfield must be in [1, 2 max_nrhs / 3]");
         return IFGF_ERR_INVALID_ARG;
     }
     return guard([&] {
         IFGF_CUDA(cudaSetDevice(plan->device));
-        apply_plan_stokes(*plan, static_cast<const float*>(forces), nfield, static_cast<float*>(out), tk,
-                          (cudaStream_t)stream, near != 0, level_mask);
+        apply_plan_stokes(*plan, forces, nfield, out, tk, (cudaStream_t)stream, near != 0, level_mask);
     });
 }
 

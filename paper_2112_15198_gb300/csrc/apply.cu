@@ -1572,6 +1572,119 @@ k_leaf_stokes_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ c
     }
 }
 
+// FP64 near field for these kernels (physical coordinates, one thread per target as k_near_f64):
+// NF force fields starting at the even field f0 + NF blockIdx.y, written to their complex slots.
+template <int NF>
+__global__ void k_near_stokes_f64(int64_t N, const int32_t* __restrict__ pboxD, const int32_t* __restrict__ startD,
+                                  const int32_t* __restrict__ nnb, const int32_t* __restrict__ nb,
+                                  const double* __restrict__ Xs, const double* __restrict__ fs,
+                                  double2* __restrict__ Is, double alpha, double c, int f0) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int f = f0 + NF * blockIdx.y;
+    const int l = pboxD[i];
+    const double xi = Xs[i], yi = Xs[N + i], zi = Xs[2 * N + i];
+    double acc[NF][3];
+#pragma unroll
+    for (int r = 0; r < NF; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.0;
+    for (int t = 0; t < nnb[l]; ++t) {
+        const int q = nb[(int64_t)l * kMaxNbr + t];
+        for (int j = startD[q]; j < startD[q + 1]; ++j) {
+            if (j == i) continue;
+            const double vx = xi - Xs[j], vy = yi - Xs[N + j], vz = zi - Xs[2 * N + j];
+            const double r2 = vx * vx + vy * vy + vz * vz;
+            const double rr = sqrt(r2);
+#pragma unroll
+            for (int r = 0; r < NF; ++r) {
+                const double* fr = fs + (int64_t)3 * (f + r) * N + j;
+                const double fx = fr[0], fy = fr[N], fz = fr[2 * N];
+                const double t3 = (vx * fx + vy * fy + vz * fz) / r2;
+                acc[r][0] += (alpha * fx + t3 * vx) / rr;
+                acc[r][1] += (alpha * fy + t3 * vy) / rr;
+                acc[r][2] += (alpha * fz + t3 * vz) / rr;
+            }
+        }
+    }
+    double2* o = Is + (int64_t)(3 * f / 2) * N + i;
+    o[0] = make_double2(c * acc[0][0], c * acc[0][1]);
+    if constexpr (NF == 2) {
+        o[N] = make_double2(c * acc[0][2], c * acc[1][0]);
+        o[2 * N] = make_double2(c * acc[1][1], c * acc[1][2]);
+    } else {
+        o[N] = make_double2(c * acc[0][2], 0.0);
+    }
+}
+
+// FP64 leaf level for these kernels (one block per leaf cone, one thread per node, as k_leaf_f64):
+// the analytic factor S(y, x')/G_0(y, x_k) = 4 pi |y - x_k| S(y, x'), then the coefficients of
+// each complex set of the block's fields.
+template <int PS, int PT, int PP, int NF>
+__global__ void k_leaf_stokes_f64(const int32_t* __restrict__ cone_box, const int32_t* __restrict__ cone_gam,
+                                  LevelGrid g, const int32_t* __restrict__ startD, const int4* __restrict__ kD,
+                                  const double* __restrict__ Xs, const double* __restrict__ fs, int64_t N, double a0,
+                                  double a1, double a2, double HD, const double* __restrict__ W,
+                                  double2* __restrict__ coef, int cstride, int nrhs, double alpha, double c, int f0) {
+    constexpr int P = PS * PT * PP;
+    constexpr int NS = NF == 2 ? 3 : 2;
+    __shared__ double2 v[NS][P], tmp[P];
+    const int cone = blockIdx.x;
+    const int f = f0 + NF * blockIdx.y;
+    const int n = threadIdx.x;
+    const int b = cone_box[cone];
+    if (n < P) {
+        const int gam = cone_gam[cone];
+        const int ip = gam % g.np, it = (gam / g.np) % g.nt, is = gam / (g.np * g.nt);
+        const int ic = n % PP, ib = (n / PP) % PT, ia = n / (PP * PT);
+        const int4 k = kD[b];
+        const double xc = a0 + (k.x + 0.5) * HD, yc = a1 + (k.y + 0.5) * HD, zc = a2 + (k.z + 0.5) * HD;
+        const double s = g.snode64[is * PS + ia], th = g.tnode64[it * PT + ib], ph = g.pnode64[ip * PP + ic];
+        const double rr = g.h64 / s;
+        const double yx = xc + rr * sin(th) * cos(ph), yy = yc + rr * sin(th) * sin(ph), yz = zc + rr * cos(th);
+        const double rk = sqrt((yx - xc) * (yx - xc) + (yy - yc) * (yy - yc) + (yz - zc) * (yz - zc));
+        double acc[NF][3];
+#pragma unroll
+        for (int r = 0; r < NF; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.0;
+        for (int j = startD[b]; j < startD[b + 1]; ++j) {
+            const double vx = yx - Xs[j], vy = yy - Xs[N + j], vz = yz - Xs[2 * N + j];
+            const double r2 = vx * vx + vy * vy + vz * vz;
+            const double dist = sqrt(r2);
+#pragma unroll
+            for (int r = 0; r < NF; ++r) {
+                const double* fr = fs + (int64_t)3 * (f + r) * N + j;
+                const double fx = fr[0], fy = fr[N], fz = fr[2 * N];
+                const double t3 = (vx * fx + vy * fy + vz * fz) / r2;
+                acc[r][0] += (alpha * fx + t3 * vx) / dist;
+                acc[r][1] += (alpha * fy + t3 * vy) / dist;
+                acc[r][2] += (alpha * fz + t3 * vz) / dist;
+            }
+        }
+        const double w = 4.0 * M_PI * rk * c;
+        v[0][n] = make_double2(w * acc[0][0], w * acc[0][1]);
+        if constexpr (NF == 2) {
+            v[1][n] = make_double2(w * acc[0][2], w * acc[1][0]);
+            v[2][n] = make_double2(w * acc[1][1], w * acc[1][2]);
+        } else {
+            v[1][n] = make_double2(w * acc[0][2], 0.0);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int sl = 0; sl < NS; ++sl) {
+        const double2 cf = cheb_coeffs_smem<PS, PT, PP>(v[sl], tmp, W, n);
+        if (n < P) coef[((int64_t)cone * nrhs + 3 * f / 2 + sl) * cstride + n] = cf;
+    }
+}
+
+// FP64 velocities back to the caller's order.
+__global__ void k_perm_out_stokes_f64(const double2* __restrict__ Is, const int32_t* __restrict__ perm, int64_t N,
+                                      double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int q = blockIdx.y;
+    const double2 v = Is[(int64_t)(q >> 1) * N + i];
+    out[(int64_t)q * N + perm[i]] = (q & 1) ? v.y : v.x;
+}
+
 // Velocities back to the caller's order: real q of the slots -> out[q][perm[i]].
 __global__ void k_perm_out_stokes(const float2* __restrict__ Is, const int32_t* __restrict__ perm, int64_t N,
                                   float* __restrict__ out) {
@@ -1773,6 +1886,41 @@ void sweep_levels_mixed(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t m
     sweep_levels_f32<PS, PT, PP>(p, nrhs, Is, s, mask);
 }
 
+// Levels D..3 of the FP64 path: interpolation to the targets of level d (Algorithm 8), then
+// propagation into level d-1 (Algorithm 7).
+template <int PS, int PT, int PP>
+void sweep_levels_f64(Plan& p, int nrhs, double2* Is, cudaStream_t s, int64_t mask) {
+    constexpr int BT = ((PS * PT * PP + 31) / 32) * 32;
+    const int64_t N = p.N;
+    const int D = p.D;
+    Level& LD = p.L[D];
+    const dim3 gN(grid_for(N, kThreads), nrhs);
+    for (int d = D; d >= 3; --d) {
+        Level& L = p.L[d];
+        const int sh = D - d;
+        const double Hd = std::ldexp(p.H1, 1 - d);
+        if ((mask >> d) & 1) {
+            TimedScope ts_(TK_INTERP, s);
+            IFGF_LAUNCH((k_interp_f64<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs, L.cs,
+                        p.off, p.Xs, L.cmap(), L.g, (const double2*)level_coef(p, d, nrhs), p.kappa, p.a[0], p.a[1],
+                        p.a[2], Hd, Is, p.cstride, nrhs, p.d_status);
+        }
+        if (d == 3) break;
+        Level& Lp = p.L[d - 1];
+        if (Lp.nc > 0) {
+            TimedScope ts_(TK_PROP, s);
+            const double2* cc = (const double2*)level_coef(p, d, nrhs);
+            double2* cp = (double2*)level_coef(p, d - 1, nrhs);
+            const int64_t cone = (int64_t)nrhs * p.cstride;
+            for_each_slice(p, d, [&](int64_t lo, int64_t n) {
+                IFGF_LAUNCH((k_prop_f64<PS, PT, PP>), dim3((unsigned)n, nrhs), BT, 0, s, Lp.cone_box + lo,
+                            Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(), L.g, cc, cp + lo * cone, sh,
+                            p.kappa, p.a[0], p.a[1], p.a[2], Hd, p.Wd, p.cstride, nrhs, p.d_status);
+            });
+        }
+    }
+}
+
 template <int PS, int PT, int PP>
 void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
     constexpr int P = PS * PT * PP;
@@ -1837,31 +1985,7 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                             LD.g, LD.start, LD.k, p.Xs, as, N, p.kappa, p.a[0], p.a[1], p.a[2], HD, p.Wd,
                             (double2*)level_coef(p, D, nrhs), p.cstride, nrhs);
             }
-        for (int d = D; d >= 3; --d) {
-            Level& L = p.L[d];
-            const int sh = D - d;
-            const double Hd = std::ldexp(p.H1, 1 - d);
-            if ((mask >> d) & 1)
-                {
-                    TimedScope ts_(TK_INTERP, s);
-                    IFGF_LAUNCH((k_interp_f64<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs,
-                                L.cs, p.off, p.Xs, L.cmap(), L.g, (const double2*)level_coef(p, d, nrhs), p.kappa, p.a[0], p.a[1],
-                                p.a[2], Hd, Is, p.cstride, nrhs, p.d_status);
-                }
-            if (d == 3) break;
-            Level& Lp = p.L[d - 1];
-            if (Lp.nc > 0) {
-                TimedScope ts_(TK_PROP, s);
-                const double2* cc = (const double2*)level_coef(p, d, nrhs);
-                double2* cp = (double2*)level_coef(p, d - 1, nrhs);
-                const int64_t cone = (int64_t)nrhs * p.cstride;
-                for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                    IFGF_LAUNCH((k_prop_f64<PS, PT, PP>), dim3((unsigned)n, nrhs), BT, 0, s, Lp.cone_box + lo,
-                                Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(), L.g, cc, cp + lo * cone, sh,
-                                p.kappa, p.a[0], p.a[1], p.a[2], Hd, p.Wd, p.cstride, nrhs, p.d_status);
-                });
-            }
-        }
+        sweep_levels_f64<PS, PT, PP>(p, nrhs, Is, s, mask);
         {
             TimedScope ts_(TK_PERM, s);
             IFGF_LAUNCH(k_perm_out<double2>, gN, kThreads, 0, s, Is, p.perm, N, (double2*)out);
@@ -1872,6 +1996,54 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
 // Apply of S = c (alpha I/r + r r^T/r^3) to nf force fields ([nf][3][N] float, caller's order)
 // into velocities (displacements) of the same layout: near field and leaf level of this kernel,
 // then the kappa = 0 level sweep on the ceil(3 nf / 2) complex slots.
+template <int PS, int PT, int PP>
+void run_apply_stokes_f64(Plan& p, const double* forces, int nf, double* vel, const TensorKernel& tk, cudaStream_t s,
+                          bool near, int64_t mask) {
+    constexpr int BT = ((PS * PT * PP + 31) / 32) * 32;
+    const int64_t N = p.N;
+    const int D = p.D;
+    Level& LD = p.L[D];
+    const int nreal = 3 * nf, slots = (nreal + 1) / 2, pairs = nf / 2;
+    double* fs = (double*)p.a_s;
+    double2* Is = (double2*)p.I_s;
+    const double c = tk.c, alpha = tk.alpha;
+    const dim3 gR(grid_for(N, kThreads), nreal);
+    {
+        TimedScope ts_(TK_PERM, s);
+        IFGF_LAUNCH(k_perm_in<double>, gR, kThreads, 0, s, forces, p.perm, N, fs);
+    }
+    if (near) {
+        TimedScope ts_(TK_NEAR, s);
+        const unsigned gx = grid_for(N, kThreads);
+        if (pairs > 0)
+            IFGF_LAUNCH(k_near_stokes_f64<2>, dim3(gx, pairs), kThreads, 0, s, N, LD.pbox, LD.start, LD.nnb, LD.nb,
+                        p.Xs, fs, Is, alpha, c, 0);
+        if (nf & 1)
+            IFGF_LAUNCH(k_near_stokes_f64<1>, dim3(gx, 1), kThreads, 0, s, N, LD.pbox, LD.start, LD.nnb, LD.nb, p.Xs,
+                        fs, Is, alpha, c, nf - 1);
+    } else {
+        IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(double2) * N * slots, s));
+    }
+    if (LD.nc > 0) {
+        TimedScope ts_(TK_LEAF, s);
+        double2* cD = (double2*)level_coef(p, D, slots);
+        const double HD = std::ldexp(p.H1, 1 - D);
+        if (pairs > 0)
+            IFGF_LAUNCH((k_leaf_stokes_f64<PS, PT, PP, 2>), dim3((unsigned)LD.nc, pairs), BT, 0, s, LD.cone_box,
+                        LD.cone_gam, LD.g, LD.start, LD.k, p.Xs, fs, N, p.a[0], p.a[1], p.a[2], HD, p.Wd, cD,
+                        p.cstride, slots, alpha, c, 0);
+        if (nf & 1)
+            IFGF_LAUNCH((k_leaf_stokes_f64<PS, PT, PP, 1>), dim3((unsigned)LD.nc, 1), BT, 0, s, LD.cone_box,
+                        LD.cone_gam, LD.g, LD.start, LD.k, p.Xs, fs, N, p.a[0], p.a[1], p.a[2], HD, p.Wd, cD,
+                        p.cstride, slots, alpha, c, nf - 1);
+    }
+    sweep_levels_f64<PS, PT, PP>(p, slots, Is, s, mask);
+    {
+        TimedScope ts_(TK_PERM, s);
+        IFGF_LAUNCH(k_perm_out_stokes_f64, gR, kThreads, 0, s, Is, p.perm, N, vel);
+    }
+}
+
 template <int PS, int PT, int PP>
 void run_apply_stokes(Plan& p, const float* forces, int nf, float* vel, const TensorKernel& tk, cudaStream_t s,
                       bool near, int64_t mask) {
@@ -1937,23 +2109,29 @@ void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, 
     }
 }
 
-void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, const TensorKernel& tk, cudaStream_t s,
+void apply_plan_stokes(Plan& p, const void* forces, int nf, void* vel, const TensorKernel& tk, cudaStream_t s,
                        bool near, int64_t mask) {
     // force fields in blocks whose ceil(3 nfb / 2) slots fit the arena's rhs_block value sets;
     // an even block size keeps every block but the last free of a half-empty slot
     int nfb = std::min(2 * p.rhs_block / 3, 21844);  // 3 nfb real sets fit a grid's y extent
     if (nfb >= 2) nfb &= ~1;
     if (nfb < 1) fail(IFGF_ERR_UNSUPPORTED, "the coefficient arena holds fewer than two value sets");
+    const bool mixed = p.precision == IFGF_PREC_MIXED;
+    const size_t rsz = mixed ? sizeof(float) : sizeof(double);
     for (int f0 = 0; f0 < nf; f0 += nfb) {
         const int nb = std::min(nfb, nf - f0);
-        const float* f = forces + (size_t)3 * f0 * p.N;
-        float* u = vel + (size_t)3 * f0 * p.N;
-        if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
-            run_apply_stokes<3, 5, 5>(p, f, nb, u, tk, s, near, mask);
-        else if (p.Ps == 5 && p.Pt == 7 && p.Pp == 7)
-            run_apply_stokes<5, 7, 7>(p, f, nb, u, tk, s, near, mask);
+        const void* f = static_cast<const char*>(forces) + (size_t)3 * f0 * p.N * rsz;
+        void* u = static_cast<char*>(vel) + (size_t)3 * f0 * p.N * rsz;
+        const bool o355 = p.Ps == 3 && p.Pt == 5 && p.Pp == 5, o577 = p.Ps == 5 && p.Pt == 7 && p.Pp == 7;
+        if (!o355 && !o577) fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
+        if (mixed && o355)
+            run_apply_stokes<3, 5, 5>(p, (const float*)f, nb, (float*)u, tk, s, near, mask);
+        else if (mixed)
+            run_apply_stokes<5, 7, 7>(p, (const float*)f, nb, (float*)u, tk, s, near, mask);
+        else if (o355)
+            run_apply_stokes_f64<3, 5, 5>(p, (const double*)f, nb, (double*)u, tk, s, near, mask);
         else
-            fail(IFGF_ERR_UNSUPPORTED, "interpolation orders not built");
+            run_apply_stokes_f64<5, 7, 7>(p, (const double*)f, nb, (double*)u, tk, s, near, mask);
     }
 }
 

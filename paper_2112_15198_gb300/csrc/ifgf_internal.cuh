@@ -268,7 +268,8 @@ struct TensorKernel {
     double c = 0.039788735772973836;  // 1/(8 pi)
     double alpha = 1.0;
 };
-void apply_plan_stokes(Plan& p, const float* forces, int nf, float* vel, const TensorKernel& tk, cudaStream_t s,
+// forces and vel: [nf][3][N] float (mixed plans) or double (FP64 plans).
+void apply_plan_stokes(Plan& p, const void* forces, int nf, void* vel, const TensorKernel& tk, cudaStream_t s,
                        bool near, int64_t mask);
 
 // =========================================================================================
