@@ -171,6 +171,30 @@ def test_higher_orders_fp64():
     assert oracle.rel_l2(_apply(gp, dens, "fp64"), exact) < 2e-6
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("kappa", [0.0, 2 * math.pi * 3])
+def test_sphere_single_layer_closed_form(prec, kappa):
+    """The single layer of unit density over a Fibonacci sphere of radius a = 1/2 at points that
+    carry no density, against its closed form: a e^{i kappa a} sin(kappa r)/(kappa r) inside,
+    a sin(kappa a) e^{i kappa r}/(kappa r) outside (a and a^2/r at kappa = 0)."""
+    n, a = 20000, 0.5
+    probes = np.array([[0.0, 0.0, 0.0], [0.1, -0.05, 0.2], [-0.2, 0.15, -0.1],
+                       [0.9, 0.3, -0.4], [-0.2, 0.6, 0.5]]).T
+    pts = np.concatenate([W.fibonacci_sphere(n), probes], axis=1)
+    dens = np.zeros((1, pts.shape[1]), dtype=np.complex128)
+    dens[0, :n] = 4 * math.pi * a * a / n
+    got = _apply(_plan(pts, kappa, precision=prec), dens, prec)[0, n:]
+    for t in range(probes.shape[1]):
+        r = float(np.linalg.norm(probes[:, t]))
+        if kappa == 0.0:
+            want = a if r < a else a * a / r
+        elif r < a:
+            want = a * np.exp(1j * kappa * a) * (np.sin(kappa * r) / (kappa * r) if r > 0 else 1.0)
+        else:
+            want = a * np.sin(kappa * a) * np.exp(1j * kappa * r) / (kappa * r)
+        assert abs(got[t] - want) <= 1e-4 * max(abs(want), 0.1), (t, got[t], want)
+
+
 def test_higher_orders_mixed():
     """Orders (5,7,7) on the mixed path (generic propagation, leaf in passes of 8 cones)."""
     pts = W.fibonacci_sphere(3000)

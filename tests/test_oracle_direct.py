@@ -6,6 +6,7 @@
 - The summation is pinned by single-source indexing, self-exclusion, reciprocity of the
   symmetric kernel, linearity, the kappa -> 0 limit, and an independent extended
   precision brute force on tiny inputs.
+- Both together by the closed form of the single layer over a sphere (a quadrature of it).
 """
 import math
 
@@ -141,3 +142,31 @@ def test_brute_force_extended_precision_tiny():
         val_re = float(np.sum(ar * re - ai * im))
         val_im = float(np.sum(ar * im + ai * re))
         assert abs(out[l] - (val_re + 1j * val_im)) < 1e-14 * max(1.0, abs(out[l]))
+
+
+def sphere_single_layer(kappa, a, x):
+    """Closed form of the single layer of unit density over the sphere |y| = a (addition theorem,
+    only the n = 0 term survives the surface integral): a e^{i kappa a} sin(kappa r)/(kappa r) for
+    r = |x| < a and a sin(kappa a) e^{i kappa r}/(kappa r) for r > a (a and a^2/r at kappa = 0)."""
+    r = float(np.linalg.norm(x))
+    if kappa == 0.0:
+        return a if r < a else a * a / r
+    if r < a:
+        return a * np.exp(1j * kappa * a) * (np.sin(kappa * r) / (kappa * r) if r > 0 else 1.0)
+    return a * np.sin(kappa * a) * np.exp(1j * kappa * r) / (kappa * r)
+
+
+@pytest.mark.parametrize("kappa", [0.0, 2 * math.pi * 3])
+def test_sphere_single_layer_closed_form(kappa):
+    """Eq. (1) as a quadrature of the single layer over a Fibonacci sphere of radius 1/2 (weights
+    area / N), seen at interior and exterior points that carry no density."""
+    n, a = 20000, 0.5
+    probes = np.array([[0.0, 0.0, 0.0], [0.1, -0.05, 0.2], [-0.2, 0.15, -0.1],
+                       [0.9, 0.3, -0.4], [-0.2, 0.6, 0.5]]).T
+    pts = np.concatenate([W.fibonacci_sphere(n), probes], axis=1)
+    dens = np.zeros(pts.shape[1], dtype=np.complex128)
+    dens[:n] = 4 * math.pi * a * a / n
+    got = oracle.direct_sum(pts, kappa, dens, np.arange(n, pts.shape[1]))[0]
+    for t in range(probes.shape[1]):
+        want = sphere_single_layer(kappa, a, probes[:, t])
+        assert abs(got[t] - want) <= 2e-5 * max(abs(want), 0.1), (t, got[t], want)
