@@ -363,11 +363,11 @@ __device__ __forceinline__ float3 node_grid(const LevelGrid& gp, int Ps, int Pt,
 // of the block are flattened over its threads (no idle lanes beyond the last round); node
 // offsets are staged in shared memory; values are summed over children in child order, then
 // the parent interpolants are generated.
-constexpr int kPropCones = 4;
-constexpr int kPropThreads = 256;
+constexpr int kPropCones = 2;
+constexpr int kPropThreads = 128;
 
 template <int PS, int PT, int PP>
-__global__ void __launch_bounds__(kPropThreads, 5)
+__global__ void __launch_bounds__(kPropThreads, 8)
 k_prop_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
            const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, LevelGrid gp,
            const int4* __restrict__ kd, ConeMap cm, LevelGrid g,
