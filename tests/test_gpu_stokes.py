@@ -231,3 +231,26 @@ def test_stokes_fp64_stages(stage):
     ref = op.apply_stokes(f, near=near, level_mask=mask)
     got = _stokes(_plan(pts, 2, precision="fp64"), f, near=near, level_mask=mask)
     _check_fields(got, ref, 1e-10)
+
+
+SMALL_CASES = {
+    "two_points": (np.array([[0.0, 1.0], [0.0, 0.5], [0.0, -0.25]]), {}),
+    "tiny": (W.random_cloud(7, seed=2), {}),
+    "one_leaf_D3": (W.random_cloud(40, seed=3), {"levels": 3}),
+    "planar": (np.stack([W.random_cloud(3000, seed=4)[0], W.random_cloud(3000, seed=5)[1], np.zeros(3000)]), {}),
+}
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("case", list(SMALL_CASES))
+def test_tensor_kernels_edge_cases(case, prec):
+    """Degenerate inputs (two points, fewer points than a leaf holds, one leaf level, a flat
+    cloud) for both tensor kernels in both precisions."""
+    pts, kw = SMALL_CASES[case]
+    f = _forces(2, pts.shape[1], 17)
+    op = oracle.Plan(pts, 0.0, levels=kw.get("levels", 0))
+    gp = _plan(pts, 2, precision=prec, **kw)
+    tol = 3e-5 if prec == "mixed" else 1e-10
+    _check_fields(_stokes(gp, f), op.apply_stokes(f), tol)
+    _check_fields(_elastic(gp, f, 0.8, 0.25), op.apply_elastic(f, 0.8, 0.25), tol)
+    assert gp.status() == 0
