@@ -520,7 +520,9 @@ constexpr int kWarpCones = 2;  // warps (parent cones) per block
 constexpr int kWarpStage = 8; // child-cone coefficient blocks staged in shared memory per warp
 constexpr int kStage4 = 39;    // float4 per staged block (38 used; odd, so lanes reading different
                                // blocks at one offset hit different banks)
-template <int PS, int PT, int PP>
+// NSETS = 1: one value set (grid row y = 0); NSETS = 0: all nrhs sets in turn, sharing the rows,
+// list entries and child-cone slots resolved once per warp.
+template <int PS, int PT, int PP, int NSETS>
 __global__ void __launch_bounds__(32 * kWarpCones, 9)
 k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ cone_gidx,
                 const int4* __restrict__ kp, const int32_t* __restrict__ pcstart, const int4* __restrict__ kd,
@@ -539,7 +541,6 @@ k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t pc = (int64_t)blockIdx.x * kWarpCones + warp;
     if (pc >= ncp) return;  // the whole warp leaves; nothing below synchronises the block
-    const int r = blockIdx.y;
     float2 (*vals)[P] = s_vals[warp];
     int (*s_slot)[kTabList] = s_slot_w[warp];
     int* s_row = s_row_w[warp];
@@ -590,6 +591,11 @@ k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_
     }
     __syncwarp();
     const int nst = min(s_koff[nch], kWarpStage);
+    const float* Ws = W;
+    const float* Wt = W + PS * PS;
+    const float* Wp = Wt + PT * PT;
+    const int nsets = NSETS ? NSETS : nrhs;
+    for (int r = 0; r < nsets; ++r) {
     for (int x = lane; x < nst * 38; x += 32) {
         const int j = x / 38, q = x - (x / 38) * 38;
         const int sl = s_dsl_w[warp][j];
@@ -636,9 +642,6 @@ k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_
             if (q < len) vals[ch][__ldg(&tab_perm[rowP + j0 + q])] = cmul(F[q], ratio[q]);
     }
     __syncwarp();
-    const float* Ws = W;
-    const float* Wt = W + PS * PS;
-    const float* Wp = Wt + PT * PT;
     for (int n = lane; n < P; n += 32) {  // sum over children, in child order
         float2 a = vals[0][n];
         for (int ch = 1; ch < nch; ++ch) {
@@ -685,6 +688,8 @@ k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_
             acc.y = fmaf(w, v.y, acc.y);
         }
         cparent[(pc * nrhs + r) * cstride + n] = acc;
+    }
+    __syncwarp();  // the next set reuses the staged blocks and the value rows
     }
 }
 
@@ -1853,10 +1858,17 @@ void sweep_levels_f32(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mas
             constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
                           TP = PS * PT * PP <= 75 ? PP : 5;
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP>), dim3((unsigned)((n + kWarpCones - 1) / kWarpCones), nrhs),
-                            32 * kWarpCones, 0, s, n, Lp.cone_box + lo, Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k,
-                            L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list, Lp.tab_perm, Lp.tab_nseg,
-                            Lp.tab_seg, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
+                const dim3 grid((unsigned)((n + kWarpCones - 1) / kWarpCones), 1);
+                if (nrhs == 1)
+                    IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP, 1>), grid, 32 * kWarpCones, 0, s, n, Lp.cone_box + lo,
+                                Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k,
+                                Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, cc, cp + lo * cone, p.Wf,
+                                p.cstride, nrhs, p.d_status);
+                else
+                    IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP, 0>), grid, 32 * kWarpCones, 0, s, n, Lp.cone_box + lo,
+                                Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k,
+                                Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, cc, cp + lo * cone, p.Wf,
+                                p.cstride, nrhs, p.d_status);
             });
         } else if (Lp.nc > 0) {
             TimedScope ts_(TK_PROP, s);
