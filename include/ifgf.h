@@ -82,6 +82,7 @@ typedef struct {
     int32_t prop_slices;   /* 0 automatic, else propagation in this many slices (>= 1) */
 } ifgf_options;
 
+/* Fill *opt with the defaults listed above, struct_size included (host only; no device call). */
 void ifgf_options_default(ifgf_options* opt);
 
 /*

@@ -146,6 +146,7 @@ def launch_count() -> int:
 def release_cached_memory() -> None:
     """Return the device memory cached by the library's memory pools (ifgf_release_cached_memory)."""
     lib = load()
+    lib.ifgf_release_cached_memory.argtypes = []
     lib.ifgf_release_cached_memory.restype = ctypes.c_int
     _check(lib.ifgf_release_cached_memory())
 

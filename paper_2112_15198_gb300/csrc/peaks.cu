@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ifgf_peaks.h"
+
 namespace {
 
 constexpr int kChains = 8;

@@ -13,8 +13,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared_functions():
-    text = open(os.path.join(ROOT, "include", "ifgf.h")).read()
+def _declared_functions(header="ifgf.h"):
+    text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"\b(ifgf_[a-z_]+)\s*\(", text)
     return sorted(set(names))
@@ -100,3 +100,42 @@ def test_invalid_options_rejected_before_any_device_work(lib):
     lib.ifgf_options_default(ctypes.byref(opt))
     opt.struct_size = 8
     assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, 1.0, None, 0, ctypes.byref(opt), None, ctypes.byref(h)) == 1
+
+
+def test_binding_declares_every_entry_point(lib):
+    """The Python binding sets argument and result types for every declared function it calls,
+    so that no pointer or double is passed through ctypes' int default."""
+    import paper_2112_15198_gb300 as ifgf
+
+    src = open(ifgf.__file__).read()
+    called = set(re.findall(r"\.(ifgf_[a-z_]+)\(", src))
+    declared = set(_declared_functions("ifgf.h")) | set(_declared_functions("ifgf_peaks.h"))
+    assert called <= declared, called - declared
+    for name in called:
+        assert f"lib.{name}.argtypes" in src, name
+
+
+def test_header_documents_every_entry_point():
+    """Each declaration in include/ifgf.h is preceded by a comment (argument meaning, layout,
+    ownership, errors), and the compute entry points cite the paper's passage."""
+    text = open(os.path.join(ROOT, "include", "ifgf.h")).read()
+    lines = text.split("\n")
+    for name in _declared_functions():
+        at = re.search(r"\n(?![ /]*\*)[a-z0-9_ *]*\b" + name + r"\s*\(", text)
+        assert at, name
+        # walk back over the declarations grouped under one comment (and their continuation lines)
+        k = text[: at.start() + 1].count("\n") - 1
+        while k >= 0 and (lines[k].strip() == "" or not lines[k].rstrip().endswith("*/")):
+            if lines[k].strip() == "};":  # an enum of the call's codes sits under the same comment
+                while k >= 0 and not lines[k].lstrip().startswith("enum"):
+                    k -= 1
+            elif not (lines[k].lstrip().startswith("#define")
+                      or not lines[k].lstrip().startswith(("*", "/*", "#", "typedef", "}", "{"))):
+                break
+            k -= 1
+        assert k >= 0 and lines[k].rstrip().endswith("*/"), f"{name} has no comment block"
+    for name, cite in (("ifgf_apply", "Algorithm"), ("ifgf_plan_create", "Sec."), ("ifgf_apply_stokes", "Sec. 2"),
+                       ("ifgf_apply_elastic", "Sec. 2")):
+        at = re.search(r"\n(?![ /]*\*)[a-z0-9_ *]*\b" + name + r"\s*\(", text).start()
+        block = text[text.rindex("/*", 0, at): at]
+        assert cite in block, (name, cite)
