@@ -68,6 +68,9 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.ifgf_plan_destroy(None) == 0
     assert lib.ifgf_apply(None, None, 1, None, None) == 1
     assert lib.ifgf_apply_stokes(None, None, 1, None, None) == 1
+    assert lib.ifgf_apply_elastic(None, None, 1, None, 1.0, 0.3, None) == 1
+    assert lib.ifgf_apply_elastic(None, None, 1, None, -1.0, 0.3, None) == 1
+    assert b"shear_modulus" in lib.ifgf_last_error()
 
 
 def test_library_links_no_torch(lib):
