@@ -95,16 +95,18 @@ void ifgf_options_default(ifgf_options* opt);
  *            caller's order.  Read only; the plan keeps its own sorted copy.
  *   N        number of points, 2 <= N < 2^31.
  *   kappa    wavenumber, finite and >= 0.
- *   orders   (P_s, P_theta, P_phi) interpolation orders, or NULL for (3, 5, 5).  This build
- *            supports (3,5,5) and (5,7,7).
+ *   orders   (P_s, P_theta, P_phi) interpolation orders (each >= 1), or NULL for (3, 5, 5).
+ *            This build has kernels for (3,5,5) and (5,7,7); other valid orders return
+ *            IFGF_ERR_UNSUPPORTED.
  *   levels   number of octree levels D in [3, 21], or 0 to choose it from leaf_target.
  *   opt      NULL for the defaults.
  *   out_plan receives the plan; unchanged on failure.
  *
  * Errors: IFGF_ERR_INVALID_ARG for N out of range, a non-finite coordinate, kappa < 0 or
- * non-finite, unsupported orders, levels outside {0} U [3, 21], all points coincident, or
- * two points sharing all three coordinates (G is singular there); IFGF_ERR_UNSUPPORTED when
- * cone_table = 1 and a level's dense cone table would exceed 2^31 entries; IFGF_ERR_OOM
+ * non-finite, an order below 1, levels outside {0} U [3, 21], all points coincident, or
+ * two points sharing all three coordinates (G is singular there); IFGF_ERR_UNSUPPORTED for
+ * orders without kernels in this build, and when cone_table = 1 and a level's dense cone
+ * table would exceed 2^31 entries; IFGF_ERR_OOM
  * (including a coefficient buffer of one density that does not fit), IFGF_ERR_CUDA.
  */
 ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, const int32_t* orders,
@@ -193,7 +195,8 @@ ifgf_status ifgf_plan_destroy(ifgf_plan plan);
  * `stream` (other buffers trigger a new capture).  Plans must live on one device, must outlive
  * the batch, and must not be applied elsewhere while the batch runs (they own their scratch).
  *
- *   plans  n plan handles (not owned).
+ *   plans  n distinct plan handles (not owned); a handle that appears twice returns
+ *          IFGF_ERR_INVALID_ARG, since each plan's buffers can serve one problem at a time.
  *   dens   n device pointers, plan i's densities as in ifgf_apply.
  *   nrhs   n counts, 1 <= nrhs[i] <= that plan's max_nrhs.
  *   outs   n device pointers, plan i's outputs.
@@ -225,7 +228,10 @@ enum {
     IFGF_Q_WORK = 13,       /* [4] near pairs, leaf pairs, level-d interpolations, level-d propagations */
     IFGF_Q_STATUS = 14,     /* [1] sticky device status (ifgf_status) */
     IFGF_Q_CHILD_START = 15, /* [n_d + 1] first child box in level d+1 */
-    IFGF_Q_BOX_COORDS = 16   /* [n_d * 3] integer box coordinates (k_x, k_y, k_z) */
+    IFGF_Q_BOX_COORDS = 16,  /* [n_d * 3] integer box coordinates (k_x, k_y, k_z) */
+    IFGF_Q_TABLES = 17       /* [1] node-table rows of level d (distinct cone indices whose node
+                                geometry seen from the children is tabled); 0 when propagation into
+                                level d computes the geometry per node */
 };
 ifgf_status ifgf_plan_query(ifgf_plan plan, int32_t what, int32_t level, int64_t* host_buf, int64_t* inout_count);
 
@@ -247,10 +253,13 @@ ifgf_status ifgf_release_cached_memory(void);
 /*
  * Opt-in live timing of the hot kernels: while enabled, every launch of a timed kernel is
  * bracketed by CUDA events on its own stream.  ifgf_timing_collect waits for the recorded
- * events, writes per-kind totals (milliseconds, launch counts) into ms[6] / launches[6]
- * (either may be NULL) and resets them.  Kinds: 0 permutations, 1 near field, 2 leaf
- * evaluation, 3 propagation, 4 interpolation, 5 whole plan construction.
+ * events, writes per-kind totals (milliseconds, launch counts) into ms[IFGF_TIMING_KINDS] /
+ * launches[IFGF_TIMING_KINDS] (either may be NULL) and resets them.  Kinds: 0 permutations,
+ * 1 near field, 2 leaf evaluation, 3 propagation into levels with node tables, 4 interpolation,
+ * 5 whole plan construction, 6 propagation into levels without node tables (the kernels compute
+ * each node's geometry; every FP64 propagation).
  */
+#define IFGF_TIMING_KINDS 7
 void ifgf_timing_enable(int32_t on);
 ifgf_status ifgf_timing_collect(double* ms, int64_t* launches);
 
@@ -277,8 +286,12 @@ ifgf_status ifgf_timing_collect(double* ms, int64_t* launches);
  * on a device looks up that array's device address (cudaGetSymbolAddress, with the device
  * current); make that first call before any stream capture.  All calls share the array and
  * each call overwrites what it reads, so calls that overlap on the GPU (two streams, or two
- * host threads) race and must be serialised by the caller.  The call returns after the
- * bounding box has been read back to the host; the keys and the sort are queued on `stream`.
+ * host threads) race and must be serialised by the caller.  Every call synchronises `stream`:
+ * it returns after the bounding box has been read back to the host, with the keys and the
+ * sort queued on `stream` behind it.  The device address found by the first call is kept for
+ * the life of the process; after a cudaDeviceReset it is stale, so this entry point must not
+ * be used on a device that has been reset.  A CUDA error left pending by the caller's earlier
+ * work (cudaGetLastError) is cleared on entry.
  * Errors: IFGF_ERR_INVALID_ARG (NULL pointer, N out of range, non-finite coordinate, all
  * points coincident), IFGF_ERR_CUDA.
  */

@@ -30,6 +30,7 @@ class Q:
     PERM, KEYS, BOX_KEYS, BOX_START, BOX_PARENT = 0, 1, 2, 3, 4
     NBR_COUNT, NBR_LIST, COUS_COUNT, COUS_LIST = 5, 6, 7, 8
     CONE_BOX, CONE_GAMMA, GRID, INFO, WORK, STATUS, CHILD_START, BOX_COORDS = 9, 10, 11, 12, 13, 14, 15, 16
+    TABLES = 17
 
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED"}
@@ -166,7 +167,7 @@ def measure_peaks() -> dict:
     return {k: float(v) for k, v in zip(keys, out)}
 
 
-TIMING_KINDS = ("perm", "near", "leaf", "prop", "interp", "plan")
+TIMING_KINDS = ("perm", "near", "leaf", "prop", "interp", "plan", "prop_gen")
 
 
 def timing_enable(on: bool = True) -> None:
@@ -176,8 +177,8 @@ def timing_enable(on: bool = True) -> None:
 
 def timing_collect() -> dict:
     """Wait for the recorded events; return {kind: (total ms, launches)} and reset."""
-    ms = (ctypes.c_double * 6)()
-    cnt = (ctypes.c_int64 * 6)()
+    ms = (ctypes.c_double * len(TIMING_KINDS))()
+    cnt = (ctypes.c_int64 * len(TIMING_KINDS))()
     _check(load().ifgf_timing_collect(ms, cnt))
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(TIMING_KINDS)}
 
@@ -273,13 +274,15 @@ class Plan:
         return tuple(int(v) for v in self.query(Q.GRID, level))
 
     def work(self) -> dict:
-        """Exact work of one apply: near pairs, leaf pairs, per-level interpolations/propagations."""
-        res = {"interp": {}, "prop": {}}
+        """Exact work of one apply: near pairs, leaf pairs, per-level interpolations/propagations;
+        "tabled"[d] tells whether the propagation out of level d reads node tables."""
+        res = {"interp": {}, "prop": {}, "tabled": {}}
         for d in range(3, self.D + 1):
             w = self.query(Q.WORK, d)
             res["near_pairs"], res["leaf_pairs"] = int(w[0]), int(w[1])
             res["interp"][d] = int(w[2])
             res["prop"][d] = int(w[3])
+            res["tabled"][d] = d > 3 and int(self.query(Q.TABLES, d - 1)[0]) > 0
         return res
 
     def destroy(self):

@@ -198,11 +198,14 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
     else if (opt.cone_table < 0 || opt.cone_table > 2) why = "cone_table must be 0, 1 or 2";
     else if (opt.prop_slices < 0 || opt.prop_slices > 4096) why = "prop_slices must be in [0, 4096]";
     else if (!(opt.tau > 0.0) || !std::isfinite(opt.tau)) why = "tau must be finite and > 0";
-    else if (!((Ps == 3 && Pt == 5 && Pp == 5) || (Ps == 5 && Pt == 7 && Pp == 7)))
-        why = "orders must be (3,5,5) or (5,7,7) in this build";
+    else if (Ps < 1 || Pt < 1 || Pp < 1) why = "orders must be >= 1";
     if (!why.empty()) {
         set_last_error(why);
         return IFGF_ERR_INVALID_ARG;
+    }
+    if (!((Ps == 3 && Pt == 5 && Pp == 5) || (Ps == 5 && Pt == 7 && Pp == 7))) {
+        set_last_error("orders other than (3,5,5) and (5,7,7) are not built");
+        return IFGF_ERR_UNSUPPORTED;
     }
     ifgf_plan_s* p = nullptr;
     ifgf_status st = guard([&] {
@@ -525,6 +528,11 @@ ifgf_status ifgf_plan_query(ifgf_plan plan, int32_t what, int32_t level, int64_t
                     for (int64_t c = 0; c < Lp.nc; ++c) prop += (int64_t)p.P * (cst[cb[c] + 1] - cst[cb[c]]);
                 }
                 res = {near, leaf, interp, prop};
+                break;
+            }
+            case IFGF_Q_TABLES: {
+                need(lev_ok && level >= 3);
+                res = {(int64_t)L.n_gam};
                 break;
             }
             case IFGF_Q_STATUS: {

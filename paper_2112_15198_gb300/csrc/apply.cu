@@ -1771,7 +1771,7 @@ void sweep_levels_mma(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mas
                             Lp.tab_perm, Lp.tab_seg, Lp.tab_run, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
             });
         } else if (Lp.nc > 0) {
-            TimedScope ts_(TK_PROP, s);
+            TimedScope ts_(TK_PROP_GEN, s);
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
                 IFGF_LAUNCH((k_prop_mma<PS, PT, PP, NT>), dim3((unsigned)n, rb), 32 * ((P + kChunk - 1) / kChunk), 0, s,
                             n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(), L.g, cc,
@@ -1871,7 +1871,7 @@ void sweep_levels_f32(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mas
                                 p.cstride, nrhs, p.d_status);
             });
         } else if (Lp.nc > 0) {
-            TimedScope ts_(TK_PROP, s);
+            TimedScope ts_(TK_PROP_GEN, s);
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
                 IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((n + kPropCones - 1) / kPropCones), nrhs),
                             kPropThreads, 0, s, n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k,
@@ -1920,7 +1920,7 @@ void sweep_levels_f64(Plan& p, int nrhs, double2* Is, cudaStream_t s, int64_t ma
         if (d == 3) break;
         Level& Lp = p.L[d - 1];
         if (Lp.nc > 0) {
-            TimedScope ts_(TK_PROP, s);
+            TimedScope ts_(TK_PROP_GEN, s);
             const double2* cc = (const double2*)level_coef(p, d, nrhs);
             double2* cp = (double2*)level_coef(p, d - 1, nrhs);
             const int64_t cone = (int64_t)nrhs * p.cstride;

@@ -55,11 +55,20 @@ ifgf_status ifgf_batch_create(const ifgf_plan* plans, int32_t n, ifgf_batch* out
         set_last_error("batch needs at least one plan and an output handle");
         return IFGF_ERR_INVALID_ARG;
     }
-    for (int32_t i = 0; i < n; ++i)
+    for (int32_t i = 0; i < n; ++i) {
         if (!plans[i]) {
             set_last_error("NULL plan in batch");
             return IFGF_ERR_INVALID_ARG;
         }
+        // a plan owns its scratch and coefficient buffers: two entries of one plan would run on
+        // concurrent branches and overwrite each other's intermediate results
+        for (int32_t j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) {
+                set_last_error("plan " + std::to_string(i) + " repeats plan " + std::to_string(j) +
+                               " of the batch");
+                return IFGF_ERR_INVALID_ARG;
+            }
+    }
     ifgf_batch_s* b = new ifgf_batch_s();
     ifgf_status st = guard_call([&] {
         for (int32_t i = 0; i < n; ++i) b->plans.push_back(plan_of(plans[i]));

@@ -232,7 +232,11 @@ inline unsigned grid_for(int64_t n, int threads) {
     } while (0)
 
 // ---- live kernel timing (opt-in; CUDA events around each hot kernel) -------------------
-enum TimingKind { TK_PERM = 0, TK_NEAR = 1, TK_LEAF = 2, TK_PROP = 3, TK_INTERP = 4, TK_PLAN = 5, TK_COUNT = 6 };
+// TK_PROP: propagation from node tables; TK_PROP_GEN: propagation that computes the node geometry.
+enum TimingKind {
+    TK_PERM = 0, TK_NEAR = 1, TK_LEAF = 2, TK_PROP = 3, TK_INTERP = 4, TK_PLAN = 5, TK_PROP_GEN = 6, TK_COUNT = 7
+};
+static_assert(TK_COUNT == IFGF_TIMING_KINDS, "timing kinds of the header");
 struct TimedScope {
     TimedScope(int kind, cudaStream_t s);
     ~TimedScope();

@@ -198,6 +198,9 @@ extern "C" ifgf_status ifgf_morton_order_noalloc(const double* points, int64_t N
         return IFGF_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // Launch errors are read back through the runtime's last-error state at the end, so an error
+    // left pending by the caller's earlier work is cleared here rather than reported as ours.
+    cudaGetLastError();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
         cudaGetLastError();

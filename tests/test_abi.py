@@ -62,9 +62,14 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert lib.ifgf_plan_create(ctypes.c_void_p(16), 1, 1.0, o, 0, None, None, ctypes.byref(h)) == 1
     assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, -1.0, o, 0, None, None, ctypes.byref(h)) == 1
     assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, 1.0, o, 2, None, None, ctypes.byref(h)) == 1
-    bad = (ctypes.c_int32 * 3)(4, 4, 4)
+    bad = (ctypes.c_int32 * 3)(0, 4, 4)
     assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, 1.0, bad, 0, None, None, ctypes.byref(h)) == 1
     assert b"orders" in lib.ifgf_last_error()
+    # valid orders without kernels in this build: unsupported, not invalid
+    for unbuilt in ((4, 4, 4), (7, 9, 9), (1, 1, 1)):
+        o2 = (ctypes.c_int32 * 3)(*unbuilt)
+        assert lib.ifgf_plan_create(ctypes.c_void_p(16), 10, 1.0, o2, 0, None, None, ctypes.byref(h)) == 6
+        assert b"orders" in lib.ifgf_last_error()
     assert lib.ifgf_plan_destroy(None) == 0
     assert lib.ifgf_apply(None, None, 1, None, None) == 1
     assert lib.ifgf_apply_stokes(None, None, 1, None, None) == 1
@@ -142,3 +147,13 @@ def test_header_documents_every_entry_point():
         at = re.search(r"\n(?![ /]*\*)[a-z0-9_ *]*\b" + name + r"\s*\(", text).start()
         block = text[text.rindex("/*", 0, at): at]
         assert cite in block, (name, cite)
+
+
+def test_batch_rejects_a_repeated_plan(lib):
+    """A plan owns its buffers, so one handle may appear once per batch; the check runs on the
+    host before any handle is dereferenced."""
+    h = ctypes.c_void_p()
+    plans = (ctypes.c_void_p * 3)(16, 32, 16)
+    assert lib.ifgf_batch_create(plans, 3, ctypes.byref(h)) == 1
+    assert b"repeats" in lib.ifgf_last_error()
+    assert lib.ifgf_batch_create(plans, 0, ctypes.byref(h)) == 1

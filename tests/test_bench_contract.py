@@ -20,7 +20,7 @@ def _work():
 def test_one_set_matches_the_per_unit_figures():
     ncone = {3: 4, 4: 5}
     f = bench.algorithmic_flops(_work(), ncone, 75, 1)
-    assert f["prop"] == 30 * 415 + 4 * 75 * 52
+    assert f["prop"] + f["prop_gen"] == 30 * 415 + 4 * 75 * 52
     assert f["interp"] == 11 * 425
     assert f["leaf"] == 200 * 35 + 5 * 75 * 52
     assert f["near"] == 100 * 22
@@ -31,6 +31,7 @@ def test_sets_repeat_only_the_per_set_work():
     one = bench.algorithmic_flops(_work(), ncone, 75, 1)
     four = bench.algorithmic_flops(_work(), ncone, 75, 4)
     assert four["prop"] - one["prop"] == 3 * (30 * 390 + 4 * 75 * 52)
+    assert four["prop_gen"] == one["prop_gen"] == 0
     assert four["interp"] - one["interp"] == 3 * 11 * 390
     assert four["near"] - one["near"] == 3 * 100 * 8
 
@@ -68,3 +69,29 @@ def test_traffic_record_is_keyed_by_the_kernel_source():
     assert sha != bench.kernel_source_sha("k_prop_warp_f32", apply_src.replace("kSegLen / 2", "kSegLen/2"), header)
     recorded = [ln for ln in open(os.path.join(ROOT, "profiles", "traffic.txt")) if ln.startswith("kernel=")]
     assert recorded and all("source_sha=" in ln for ln in recorded)
+
+
+def test_propagation_split_by_node_tables():
+    """Evaluations out of level d, and the coefficients of the level-(d-1) cones they produce,
+    belong to the node-table kernel when level d-1 has tables, else to the generic one."""
+    work = {"prop": {3: 0, 4: 20, 5: 7}, "interp": {3: 5, 4: 6, 5: 1}, "near_pairs": 1, "leaf_pairs": 2,
+            "tabled": {3: False, 4: False, 5: True}}
+    ncone = {3: 4, 4: 5, 5: 6}
+    f = bench.algorithmic_flops(work, ncone, 75, 1)
+    assert f["prop_gen"] == 20 * 415 + 4 * 75 * 52
+    assert f["prop"] == 7 * 415 + 5 * 75 * 52
+
+
+def test_roofline_reports_every_kernel_kind():
+    kt = {"perm": (1.0, 4), "near": (2.0, 2), "leaf": (3.0, 2), "prop": (10.0, 6), "interp": (4.0, 12),
+          "plan": (5.0, 2), "prop_gen": (8.0, 4)}
+    flops = {"near": 2e9, "leaf": 3e9, "prop": 1e10, "prop_gen": 4e9, "interp": 5e9}
+    peaks = {"fp32_ffma_tflops": 78.0, "fp32x2_ffma2_tflops": 80.0, "fp64_tflops": 1.2, "mufu_sin_gops": 5e3,
+             "tf32_mma_sync_tflops": 300.0, "sms": 152.0}
+    r = bench.roofline_of(kt, flops, 2, "mixed", False, False, peaks)
+    assert set(r["per_kernel"]) == {"near", "leaf", "prop", "prop_gen", "interp"}
+    assert r["kernel"] == "k_prop_warp_f32" and r["per_kernel"]["prop_gen"]["kernel"] == "k_prop_f32"
+    # 1e10 flops per step x 2 steps in 10 ms
+    assert abs(r["achieved"] - 2.0) < 1e-12 and abs(r["frac"] - 2.0 / 80.0) < 1e-12
+    m = bench.roofline_of(kt, flops, 2, "mixed", False, True, peaks)
+    assert m["bound"] == "tensor" and abs(m["peak"] - 100.0) < 1e-12

@@ -208,7 +208,8 @@ def test_higher_orders_mixed():
         assert oracle.rel_l2(got[r], ref[r]) < 3e-5
 
 
-@pytest.mark.parametrize("what", ["duplicate", "nan", "n1", "kappa", "levels", "orders", "host_points"])
+@pytest.mark.parametrize("what", ["duplicate", "nan", "n1", "kappa", "levels", "orders", "host_points",
+                                  "unbuilt_orders"])
 def test_invalid_input_rejected(what):
     pts = W.random_cloud(100, seed=1)
     kw = {}
@@ -224,13 +225,15 @@ def test_invalid_input_rejected(what):
     elif what == "levels":
         kw["levels"] = 22
     elif what == "orders":
-        kw["orders"] = (4, 4, 4)
+        kw["orders"] = (0, 4, 4)
+    elif what == "unbuilt_orders":
+        kw["orders"] = (7, 9, 9)  # valid orders without kernels in this build
     with pytest.raises(ifgf.IFGFError) as e:
         if what == "host_points":
             ifgf.Plan(torch.from_numpy(pts), kappa)
         else:
             _plan(pts, kappa, **kw)
-    assert e.value.status == 1
+    assert e.value.status == (6 if what == "unbuilt_orders" else 1)
 
 
 def test_nrhs_limit():
