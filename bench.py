@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--workload", default="sphere512")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--study", default="", choices=["", "linearithmic"],
+                    help="linearithmic: plan + apply time and error against N log N for four sizes of the "
+                         "sphere and the prolate spheroid (fixed sampling density)")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the FP64 GPU and kappa = 0 records beside the line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -443,11 +446,62 @@ def side_record(torch, ifgf, args, name, precision, P_dev, stream, flush, steps,
     return rec
 
 
+def run_linearithmic(args):
+    """Cost against N at a fixed sampling density (the GPU counterpart of the paper's study of
+    linearithmic scaling): for each body and size, plan + apply and apply alone (CUDA events, L2
+    flushed, mean of the timed steps after the warm-up) and the error on 200 seeded targets."""
+    import torch
+
+    import oracle
+    import paper_2112_15198_gb300 as ifgf
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for body in ("sphere", "prolate"):
+        for w in W.linearithmic_series(body):
+            pts = w.points()
+            dens = w.densities()
+            P = torch.from_numpy(pts).to(dev)
+            A = torch.from_numpy(dens).to(dev).to(torch.complex64)
+            out = torch.empty_like(A)
+
+            def step():
+                plan = ifgf.Plan(P, w.kappa)
+                plan.apply(A, out)
+                plan.destroy()
+
+            for _ in range(max(1, args.warmup)):
+                step()
+            st = statistics.mean(timed_steps(torch, stream, flush, step, max(1, args.steps)))
+            plan = ifgf.Plan(P, w.kappa)
+            plan.apply(A, out)
+            ap = statistics.mean(timed_steps(torch, stream, flush, lambda: plan.apply(A, out), max(1, args.steps)))
+            D = plan.D
+            plan.destroy()
+            tg = w.targets()
+            err = rel_l2(out.cpu().numpy().astype(np.complex128)[:, tg], oracle.direct_sum(pts, w.kappa, dens, tg))
+            nlogn = w.n * math.log2(w.n)
+            rows.append({"body": body, "N": w.n, "wavelengths": w.wavelengths, "levels": D,
+                         "ms_plan_apply": st, "ms_apply": ap, "ns_apply_per_NlogN": ap * 1e6 / nlogn,
+                         "ns_step_per_NlogN": st * 1e6 / nlogn, "rel_err": err, "targets": int(tg.shape[0])})
+            del P, A, out
+    print(json.dumps({"study": "linearithmic", "metric": "apply time / (N log2 N)", "unit": "ns",
+                      "steps": args.steps, "warmup": args.warmup, "precision": "mixed", "orders": [3, 5, 5],
+                      "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.study == "linearithmic":
+        if rank == 0:
+            run_linearithmic(args)
         return
     import torch
 
@@ -540,14 +594,24 @@ def main():
     d2h = out_host.numel() * out_host.element_size()
     del Pd, Ad, out_host
 
-    # ---- the plain FP64 GPU IFGF and the kappa = 0 repeat on the same points ----------
+    # ---- the kappa = 0 repeat on the same points; the plain FP64 GPU IFGF against the mixed one --
     extra = {}
     if rank == 0 and not args.no_side and args.kernel == "helmholtz" and args.precision == "mixed":
-        if w.nrhs == 1:
-            extra["fp64_gpu"] = side_record(torch, ifgf, args, args.workload, "fp64", P, stream, flush, 1, 0)
         if w.wavelengths > 0 and f"{args.workload}_laplace" in W.WORKLOADS:
             extra["laplace"] = side_record(torch, ifgf, args, f"{args.workload}_laplace", "mixed", P, stream, flush,
                                            side, 1)
+        if w.nrhs == 1:
+            # The FP64 coefficients of one level of the 512-wavelength sphere (about 2.4e8 cones of
+            # 75 complex128) exceed the device memory, so the two precisions are compared on the
+            # largest workload where both fit, the 64-wavelength sphere, one plan + apply each.
+            del P
+            torch.cuda.empty_cache()
+            fw = "sphere64" if w.n > 1_572_864 else args.workload
+            Pf = torch.from_numpy(W.make(fw).points()).to(dev)
+            extra["fp64_vs_mixed"] = {
+                "fp64": side_record(torch, ifgf, args, fw, "fp64", Pf, stream, flush, 1, 1),
+                "mixed": side_record(torch, ifgf, args, fw, "mixed", Pf, stream, flush, side, 1)}
+            del Pf
 
     if rank != 0:
         if pg:

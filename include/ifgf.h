@@ -235,6 +235,90 @@ enum {
 };
 ifgf_status ifgf_plan_query(ifgf_plan plan, int32_t what, int32_t level, int64_t* host_buf, int64_t* inout_count);
 
+/*
+ * Distribution over several GPUs (Sec. 3.2), one rank per GPU.
+ *
+ * ifgf_partition_boxes: the Morton-ordered leaf boxes in nranks intervals with point counts as
+ *   close as possible to N / nranks (Sec. 3.2.1): bound r is the box boundary whose point offset
+ *   box_start[b] is nearest to r N / nranks (the lower one on a tie), non-decreasing; rank r owns
+ *   boxes [out_bounds[r], out_bounds[r+1]).  box_start: host, [nbox + 1] sorted point offsets
+ *   (box_start[0] = 0, non-decreasing); out_bounds: host, [nranks + 1].  Host only.
+ * ifgf_partition_cones: a level's nc relevant cones, in the cone order of Sec. 3.2.1, in nranks
+ *   contiguous intervals of nearly equal size (co-centred cones may fall to different ranks):
+ *   out_bounds[r] = floor(r nc / nranks).  Host only.
+ * Errors: IFGF_ERR_INVALID_ARG for NULL arrays, nranks < 1, nbox < 1 or nc < 0, or ranges that do
+ * not start at 0 or decrease.
+ */
+ifgf_status ifgf_partition_boxes(const int64_t* box_start, int64_t nbox, int32_t nranks, int64_t* out_bounds);
+ifgf_status ifgf_partition_cones(int64_t nc, int32_t nranks, int64_t* out_bounds);
+
+typedef struct ifgf_shard_s* ifgf_shard;
+/*
+ * One rank's part of a plan (Sec. 3.2): it owns the points of an interval of leaf boxes and, at
+ * every level, an interval of the relevant cones (the partitions above), and it holds
+ * coefficients only for its own cones and for the cones of other ranks its steps read.  Those are
+ * the cones its points look up in Interpolation(d) and the child cones its parent cones look up in
+ * Propagation(d) (Algorithms 7 and 8 restricted to the rank; the data of the paper's two
+ * communication algorithms).  Every rank builds the same plan from the same points; the shard
+ * borrows it (the plan must outlive the shard and must not be applied while shard steps run).
+ * Mixed-precision plans, up to max_nrhs <= 3 value sets per step.  Synchronous.
+ *
+ * An apply on a rank runs, on `stream`:
+ *   ifgf_shard_near_leaf   the near field of its points and LevelDEvaluations of its level-D cones;
+ *   for d = D .. 3:
+ *     (the caller fills the level-d blocks of the cones in IFGF_SQ_NEED_CONES, in that order,
+ *      after the rank's own blocks in ifgf_shard_coefficients' buffer, from their owners'
+ *      buffers: ifgf_shard_pack on the owner, then any transport)
+ *     ifgf_shard_level(d)  Interpolation(d) of its points, then (d > 3) Propagation(d) of its
+ *                          level-(d-1) cones into its own level-(d-1) blocks.
+ * Densities and results are [nrhs][N] complex64 vectors in the sorted point order (ifgf_permute
+ * converts); a rank reads the densities of its points and of IFGF_SQ_NEED_POINTS, and writes the
+ * results of its own points only (the near field sets them, the levels add to them).  A rank's
+ * results are bit-identical to those of ifgf_apply on the same points.
+ *
+ *   ifgf_shard_create       plan, nranks >= 1, 0 <= rank < nranks, 1 <= max_nrhs <= 3.
+ *   ifgf_shard_query        as ifgf_plan_query, with the IFGF_SQ_* items below.
+ *   ifgf_shard_coefficients device pointer of the level's buffer (own blocks, then the needed
+ *                           ones) and the bytes of one cone block at nrhs value sets.
+ *   ifgf_shard_pack         dst (device) <- the rank's own level blocks of the n cones ids
+ *                           (device, int64, each within the rank's own interval), in that order.
+ *   ifgf_shard_unpack       the n blocks at src (device) become needed cones first .. first + n - 1
+ *                           (positions in IFGF_SQ_NEED_CONES) of the level's buffer.
+ * Errors: IFGF_ERR_INVALID_ARG (NULL handle or buffer, rank, level or nrhs out of range),
+ * IFGF_ERR_UNSUPPORTED (an FP64 plan), IFGF_ERR_OOM, IFGF_ERR_CUDA, and IFGF_ERR_INTERNAL from
+ * ifgf_shard_create when a lookup finds no relevant cone.
+ */
+enum {
+    IFGF_SQ_POINTS = 0,         /* [2] first and end sorted point of the rank */
+    IFGF_SQ_BOXES = 1,          /* [2] first and end leaf box of the rank */
+    IFGF_SQ_CONES = 2,          /* [2] first and end relevant cone of the rank at `level` */
+    IFGF_SQ_NEED_CONES = 3,     /* [m] cones of other ranks read at `level`, ascending */
+    IFGF_SQ_NEED_POINTS = 4,    /* [m] sorted points of other ranks read, ascending */
+    IFGF_SQ_POINT_BOUNDS = 5,   /* [nranks + 1] sorted point intervals of all ranks */
+    IFGF_SQ_CONE_BOUNDS = 6,    /* [nranks + 1] cone intervals of all ranks at `level` */
+    IFGF_SQ_LOOKED_INTERP = 7,  /* [m] cones the rank's Interpolation(level) looks up (own ones too) */
+    IFGF_SQ_LOOKED_PROP = 8     /* [m] cones the rank's Propagation(level) looks up (own ones too) */
+};
+ifgf_status ifgf_shard_create(ifgf_plan plan, int32_t nranks, int32_t rank, int32_t max_nrhs, ifgf_shard* out);
+ifgf_status ifgf_shard_query(ifgf_shard shard, int32_t what, int32_t level, int64_t* host_buf, int64_t* inout_count);
+ifgf_status ifgf_shard_coefficients(ifgf_shard shard, int32_t level, int32_t nrhs, void** buf, int64_t* block_bytes);
+ifgf_status ifgf_shard_pack(ifgf_shard shard, int32_t level, int32_t nrhs, const int64_t* ids, int64_t n, void* dst,
+                            void* stream);
+ifgf_status ifgf_shard_unpack(ifgf_shard shard, int32_t level, int32_t nrhs, const void* src, int64_t first, int64_t n,
+                              void* stream);
+ifgf_status ifgf_shard_near_leaf(ifgf_shard shard, const void* dens_sorted, int32_t nrhs, void* out_sorted,
+                                 void* stream);
+ifgf_status ifgf_shard_level(ifgf_shard shard, int32_t level, int32_t nrhs, void* out_sorted, void* stream);
+ifgf_status ifgf_shard_destroy(ifgf_shard shard);
+
+/*
+ * Reorder [nrhs][N] complex vectors of the plan's precision (complex64 MIXED, complex128 FP64)
+ * between the caller's point order and the plan's sorted order (Sec. 3.2.1): to_sorted != 0 gives
+ * out[r][i] = in[r][perm[i]], else out[r][perm[i]] = in[r][i].  Device buffers, asynchronous on
+ * `stream`; out must not alias in.  Errors: IFGF_ERR_INVALID_ARG.
+ */
+ifgf_status ifgf_permute(ifgf_plan plan, const void* in, int32_t nrhs, void* out, int32_t to_sorted, void* stream);
+
 /* Text of a status code, and the calling thread's last error detail. */
 const char* ifgf_status_string(ifgf_status s);
 const char* ifgf_last_error(void);
@@ -262,6 +346,24 @@ ifgf_status ifgf_release_cached_memory(void);
 #define IFGF_TIMING_KINDS 7
 void ifgf_timing_enable(int32_t on);
 ifgf_status ifgf_timing_collect(double* ms, int64_t* launches);
+
+/*
+ * Fault injection for tests.  Neither call is needed in normal use.
+ *
+ * ifgf_debug_fail_allocation(n): for n >= 1, the n-th device allocation the library makes from
+ * now on (in any plan) fails as if the device were out of memory, once; n = 0 turns the hook
+ * off.  The failing call returns IFGF_ERR_OOM after releasing everything it had allocated.
+ *
+ * ifgf_debug_drop_cone(plan, level, cone): removes relevant cone `cone` (an index of
+ * IFGF_Q_CONE_BOX at `level`) from the level's dense cone table, so that every lookup of it by
+ * the apply misses.  The kernels then treat its coefficients as zero and record
+ * IFGF_ERR_INTERNAL in the plan's status (ifgf_plan_query(IFGF_Q_STATUS)); no memory outside
+ * the plan's buffers is touched.  The plan stays usable but its results are no longer those of
+ * the method.  Synchronous.  Errors: IFGF_ERR_INVALID_ARG (NULL plan, level or cone out of
+ * range), IFGF_ERR_UNSUPPORTED (the level keeps sorted cone lists instead of a dense table).
+ */
+void ifgf_debug_fail_allocation(int64_t n);
+ifgf_status ifgf_debug_drop_cone(ifgf_plan plan, int32_t level, int64_t cone);
 
 /*
  * Allocation-free Morton order of N points.  The paper has no counterpart: this entry point

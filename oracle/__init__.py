@@ -15,6 +15,9 @@ S2  ``Plan.apply_stokes``: the O2 IFGF for the Stokeslet on a kappa = 0 plan.
 E1  ``elastic_direct_sum``: Eq. (1) with Kelvin's solution of linear elasticity
     (shear modulus mu, Poisson ratio nu), pair by pair in FP64.
 E2  ``Plan.apply_elastic``: the O2 IFGF for Kelvin's solution on a kappa = 0 plan.
+M1  ``partition_boxes``, ``partition_cones``, ``Plan.shard_cones``, ``Plan.shard_points``: the
+    distribution of Sec. 3.2 (points by intervals of leaf boxes, cones by intervals of the cone
+    order) and the data one rank reads from the others.
 
 Parity unpinned: none of the functions here lacks a pin; see ``tests/test_oracle_*``.
 """
@@ -96,6 +99,10 @@ def _load():
         lib.orc_cheb_nodes.argtypes = [c_vp, c_vp, c_vp, c_vp]
         lib.orc_has_duplicates.argtypes = [c_vp]
         lib.orc_has_duplicates.restype = c_int
+        lib.orc_shard_cones.argtypes = [c_vp, c_int, c_i64, c_i64, c_i64, c_i64, c_vp]
+        lib.orc_shard_cones.restype = c_int
+        lib.orc_shard_points.argtypes = [c_vp, c_i64, c_i64, c_i64, c_i64, c_vp]
+        lib.orc_shard_points.restype = None
         lib.orc_set_threads.argtypes = [c_int]
         lib.orc_max_threads.restype = c_int
         _lib = lib
@@ -280,6 +287,26 @@ class Plan:
             raise OracleError(f"orc_apply_elastic failed with status {st}")
         return out
 
+    def shard_cones(self, level: int, points: tuple, parent_cones: tuple) -> np.ndarray:
+        """M1: per level-`level` cone, bit 0 set when Interpolation(level) of the sorted points
+        [points[0], points[1]) looks it up, bit 1 when Propagation(level) of the level-(level-1) cones
+        [parent_cones[0], parent_cones[1]) does (the data a rank gathers from others, Sec. 3.2.3)."""
+        out = np.zeros(max(self.ncone[level], 1), dtype=np.uint8)
+        st = self._lib.orc_shard_cones(self._h, int(level), int(points[0]), int(points[1]), int(parent_cones[0]),
+                                       int(parent_cones[1]), _ptr(out))
+        if st != 0:
+            raise OracleError(f"orc_shard_cones failed with status {st}")
+        return out[: self.ncone[level]]
+
+    def shard_points(self, points: tuple, leaf_cones: tuple) -> np.ndarray:
+        """M1: per sorted point, bit 0 set when the near field of the sorted points [points[0],
+        points[1]) reads it, bit 1 when LevelDEvaluations of the level-D cones [leaf_cones[0],
+        leaf_cones[1]) does."""
+        out = np.zeros(self.N, dtype=np.uint8)
+        self._lib.orc_shard_points(self._h, int(points[0]), int(points[1]), int(leaf_cones[0]), int(leaf_cones[1]),
+                                   _ptr(out))
+        return out
+
     def work(self) -> dict:
         """Exact work counters of the last apply: near pairs, leaf pairs, per-level evaluations."""
         w0 = self.get(Q_WORK, self.D)
@@ -289,6 +316,29 @@ class Plan:
             res["interp"][d] = int(w[2])
             res["prop"][d] = int(w[3])
         return res
+
+
+def partition_boxes(box_start: np.ndarray, nranks: int) -> np.ndarray:
+    """Sec. 3.2.1: the Morton-ordered leaf boxes in nranks intervals whose point counts are as close
+    as possible to N / nranks.  Reading: bound r is the box boundary whose point offset is nearest
+    to r N / nranks (the lower one on a tie), non-decreasing in r; rank r owns boxes
+    [bound r, bound r+1)."""
+    box_start = np.asarray(box_start, dtype=np.int64)
+    nbox = box_start.shape[0] - 1
+    n = int(box_start[-1])
+    bounds = [0]
+    for r in range(1, nranks):
+        t = n * r / nranks
+        best = min(range(nbox + 1), key=lambda b: (abs(box_start[b] - t), b))
+        bounds.append(max(best, bounds[-1]))
+    bounds.append(nbox)
+    return np.array(bounds, dtype=np.int64)
+
+
+def partition_cones(nc: int, nranks: int) -> np.ndarray:
+    """Sec. 3.2.1: a level's relevant cones, in cone order, in nranks contiguous intervals of
+    (nearly) equal size: rank r owns [floor(r nc / nranks), floor((r + 1) nc / nranks))."""
+    return np.array([nc * r // nranks for r in range(nranks + 1)], dtype=np.int64)
 
 
 def rel_l2(approx: np.ndarray, exact: np.ndarray) -> float:

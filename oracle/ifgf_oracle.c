@@ -20,6 +20,9 @@
  *   S2  orc_apply_stokes    the same IFGF steps for the Stokeslet on a kappa = 0 plan.
  *   E1  orc_elastic_direct_sum  Eq. (1) with Kelvin's solution of linear elasticity.
  *   E2  orc_apply_elastic   the IFGF steps for Kelvin's solution on a kappa = 0 plan.
+ *   M1  orc_shard_cones, orc_shard_points   the data one rank of a distributed run reads
+ *                           (Sec. 3.2): the cones its Interpolation and Propagation look up and
+ *                           the points its near field and LevelDEvaluations read.
  *
  * The paper defers the numerical details of IFGF (analytic factor, the
  * singularity-resolving radial variable, interpolation nodes, cone counts) to
@@ -1060,6 +1063,87 @@ enum {
     ORC_Q_WORK = 12,
     ORC_Q_CHILD_START = 13,
 };
+
+/* ------------------------------------------------------------------------- */
+/* Distribution over ranks (Sec. 3.2): what one rank reads                     */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The level-d cones a rank reads, for the rank that owns the sorted points [pt_lo, pt_hi) and the
+ * level-(d-1) relevant cones [pc_lo, pc_hi).  need[c] (c a level-d cone index) receives
+ *   bit 0  when Interpolation(d) of one of the rank's points looks the cone up: for each point x
+ *          and each box B in M^d(x) (the cousins of x's level-d box), the cone of B containing x
+ *          (the lookups of Algorithm 8 whose data CommunicateInterpolationData gathers);
+ *   bit 1  when Propagation(d) of one of the rank's parent cones looks it up: for each parent cone,
+ *          each relevant child box of its box and each interpolation node, the child cone
+ *          containing the node (the lookups of Algorithm 7 gathered by CommunicatePropagationData).
+ * need is cleared first.  Returns 0, or ORC_ERR_INTERNAL when a lookup finds no relevant cone.
+ */
+int orc_shard_cones(const orc_plan* p, int d, int64_t pt_lo, int64_t pt_hi, int64_t pc_lo, int64_t pc_hi,
+                    unsigned char* need) {
+    if (d < 3 || d > p->D) return ORC_ERR_ARG;
+    const orc_level* L = &p->L[d];
+    const orc_grid* g = &L->g;
+    memset(need, 0, (size_t)L->nc);
+    int bad = 0;
+    for (int64_t i = pt_lo; i < pt_hi; ++i) {
+        const int64_t A = L->pbox[i];
+        for (int t = 0; t < L->ncs[A]; ++t) {
+            const int64_t B = L->cs[A * MAX_COUS + t];
+            float v[3];
+            point_grid_offset(p, d, i, B, v);
+            const int64_t cone = L->slot[B * g->C + classify(g, v[0], v[1], v[2])];
+            if (cone < 0) bad = 1;
+            else need[cone] |= 1;
+        }
+    }
+    if (d > 3) {
+        const orc_level* Lp = &p->L[d - 1];
+        for (int64_t pc = pc_lo; pc < pc_hi; ++pc) {
+            const int64_t jb = Lp->cone_box[pc];
+            const int32_t* kp = &Lp->k[3 * jb];
+            for (int64_t kb = Lp->cstart[jb]; kb < Lp->cstart[jb + 1]; ++kb) {
+                const int32_t* kk = &L->k[3 * kb];
+                float o[3];
+                for (int c = 0; c < 3; ++c)
+                    o[c] = (float)(((int64_t)2 * (kk[c] - 2 * kp[c]) - 1) * ((int64_t)1 << (p->D - d)));
+                for (int a = 0; a < p->Ps; ++a)
+                    for (int b = 0; b < p->Pt; ++b)
+                        for (int c = 0; c < p->Pp; ++c) {
+                            float q[3];
+                            node_grid(p, &Lp->g, Lp->cone_gam[pc], a, b, c, q);
+                            const int64_t cone = L->slot[kb * g->C + classify(g, q[0] - o[0], q[1] - o[1], q[2] - o[2])];
+                            if (cone < 0) bad = 1;
+                            else need[cone] |= 2;
+                        }
+            }
+        }
+    }
+    return bad ? ORC_ERR_INTERNAL : ORC_OK;
+}
+
+/*
+ * The sorted points a rank reads besides its own, for the rank that owns the sorted points
+ * [pt_lo, pt_hi) and the level-D relevant cones [c_lo, c_hi): need[i] receives bit 0 for the
+ * points of the level-D neighbours of its points' boxes (the near field, Sec. 2) and bit 1 for the
+ * points of the boxes of its level-D cones (LevelDEvaluations, Algorithm 6); need is cleared first.
+ */
+void orc_shard_points(const orc_plan* p, int64_t pt_lo, int64_t pt_hi, int64_t c_lo, int64_t c_hi,
+                      unsigned char* need) {
+    const orc_level* LD = &p->L[p->D];
+    memset(need, 0, (size_t)p->N);
+    for (int64_t i = pt_lo; i < pt_hi; ++i) {
+        const int64_t b = LD->pbox[i];
+        for (int t = 0; t < LD->nnb[b]; ++t) {
+            const int64_t q = LD->nb[b * MAX_NBR + t];
+            for (int64_t j = LD->start[q]; j < LD->start[q + 1]; ++j) need[j] |= 1;
+        }
+    }
+    for (int64_t c = c_lo; c < c_hi; ++c) {
+        const int64_t b = LD->cone_box[c];
+        for (int64_t j = LD->start[b]; j < LD->start[b + 1]; ++j) need[j] |= 2;
+    }
+}
 
 /* Copies an integer array of the plan into buf (int64) when buf != NULL; returns its length. */
 int64_t orc_get(const orc_plan* p, int what, int d, int64_t* buf) {

@@ -18,6 +18,7 @@ import numpy as np
 from . import _build
 
 __all__ = ["IFGFError", "Plan", "Batch", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q",
+           "debug_fail_allocation", "Shard", "SQ", "partition_boxes", "partition_cones",
            "PREC_FP64", "PREC_MIXED"]
 
 PREC_FP64 = 0
@@ -108,6 +109,32 @@ def load(build: bool = True):
         lib.ifgf_batch_apply.restype = ctypes.c_int
         lib.ifgf_batch_destroy.argtypes = [vp]
         lib.ifgf_batch_destroy.restype = ctypes.c_int
+        lib.ifgf_debug_fail_allocation.argtypes = [i64]
+        lib.ifgf_debug_fail_allocation.restype = None
+        lib.ifgf_debug_drop_cone.argtypes = [vp, i32, i64]
+        lib.ifgf_debug_drop_cone.restype = ctypes.c_int
+        lib.ifgf_partition_boxes.argtypes = [ctypes.POINTER(i64), i64, i32, ctypes.POINTER(i64)]
+        lib.ifgf_partition_boxes.restype = ctypes.c_int
+        lib.ifgf_partition_cones.argtypes = [i64, i32, ctypes.POINTER(i64)]
+        lib.ifgf_partition_cones.restype = ctypes.c_int
+        lib.ifgf_shard_create.argtypes = [vp, i32, i32, i32, ctypes.POINTER(vp)]
+        lib.ifgf_shard_create.restype = ctypes.c_int
+        lib.ifgf_shard_query.argtypes = [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.ifgf_shard_query.restype = ctypes.c_int
+        lib.ifgf_shard_coefficients.argtypes = [vp, i32, i32, ctypes.POINTER(vp), ctypes.POINTER(i64)]
+        lib.ifgf_shard_coefficients.restype = ctypes.c_int
+        lib.ifgf_shard_pack.argtypes = [vp, i32, i32, vp, i64, vp, vp]
+        lib.ifgf_shard_pack.restype = ctypes.c_int
+        lib.ifgf_shard_unpack.argtypes = [vp, i32, i32, vp, i64, i64, vp]
+        lib.ifgf_shard_unpack.restype = ctypes.c_int
+        lib.ifgf_shard_near_leaf.argtypes = [vp, vp, i32, vp, vp]
+        lib.ifgf_shard_near_leaf.restype = ctypes.c_int
+        lib.ifgf_shard_level.argtypes = [vp, i32, i32, vp, vp]
+        lib.ifgf_shard_level.restype = ctypes.c_int
+        lib.ifgf_shard_destroy.argtypes = [vp]
+        lib.ifgf_shard_destroy.restype = ctypes.c_int
+        lib.ifgf_permute.argtypes = [vp, vp, i32, vp, i32, vp]
+        lib.ifgf_permute.restype = ctypes.c_int
         lib.ifgf_timing_enable.argtypes = [i32]
         lib.ifgf_timing_enable.restype = None
         lib.ifgf_timing_collect.argtypes = [ctypes.POINTER(dbl), ctypes.POINTER(i64)]
@@ -150,6 +177,90 @@ def release_cached_memory() -> None:
     lib.ifgf_release_cached_memory.argtypes = []
     lib.ifgf_release_cached_memory.restype = ctypes.c_int
     _check(lib.ifgf_release_cached_memory())
+
+
+def debug_fail_allocation(n: int) -> None:
+    """Fault injection for tests: the n-th device allocation from now on fails as out of memory
+    (ifgf_debug_fail_allocation); 0 turns it off."""
+    load().ifgf_debug_fail_allocation(int(n))
+
+
+def partition_boxes(box_start, nranks: int) -> np.ndarray:
+    """Leaf-box intervals of the ranks (ifgf_partition_boxes, Sec. 3.2.1); host only."""
+    bs = np.ascontiguousarray(box_start, dtype=np.int64)
+    out = np.zeros(int(nranks) + 1, dtype=np.int64)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    _check(load().ifgf_partition_boxes(bs.ctypes.data_as(i64p), bs.shape[0] - 1, int(nranks), out.ctypes.data_as(i64p)))
+    return out
+
+
+def partition_cones(nc: int, nranks: int) -> np.ndarray:
+    """Cone intervals of the ranks at one level (ifgf_partition_cones, Sec. 3.2.1); host only."""
+    out = np.zeros(int(nranks) + 1, dtype=np.int64)
+    _check(load().ifgf_partition_cones(int(nc), int(nranks), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out
+
+
+class SQ:
+    """Query codes of ifgf_shard_query."""
+
+    POINTS, BOXES, CONES, NEED_CONES, NEED_POINTS, POINT_BOUNDS, CONE_BOUNDS, LOOKED_INTERP, LOOKED_PROP = range(9)
+
+
+class Shard:
+    """One rank's part of a plan (ifgf_shard_create, Sec. 3.2); see sharding.py for the apply."""
+
+    def __init__(self, plan, nranks: int, rank: int, max_nrhs: int = 1):
+        lib = load()
+        self._lib = lib
+        self.plan = plan  # the shard borrows the plan
+        self.nranks, self.rank, self.max_nrhs = int(nranks), int(rank), int(max_nrhs)
+        h = ctypes.c_void_p()
+        _check(lib.ifgf_shard_create(plan._h, self.nranks, self.rank, self.max_nrhs, ctypes.byref(h)))
+        self._h = h
+
+    def query(self, what: int, level: int = 0) -> np.ndarray:
+        cnt = ctypes.c_int64(0)
+        _check(self._lib.ifgf_shard_query(self._h, int(what), int(level), None, ctypes.byref(cnt)))
+        buf = np.zeros(max(cnt.value, 1), dtype=np.int64)
+        cnt2 = ctypes.c_int64(buf.shape[0])
+        _check(self._lib.ifgf_shard_query(self._h, int(what), int(level),
+                                          buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(cnt2)))
+        return buf[: cnt.value]
+
+    def block_bytes(self, level: int, nrhs: int) -> int:
+        ptr, nb = ctypes.c_void_p(), ctypes.c_int64(0)
+        _check(self._lib.ifgf_shard_coefficients(self._h, int(level), int(nrhs), ctypes.byref(ptr), ctypes.byref(nb)))
+        return int(nb.value)
+
+    def pack(self, level: int, nrhs: int, ids, dst, stream=None):
+        """dst <- the rank's own blocks of the cones ids (int64 device tensor), in that order."""
+        _check(self._lib.ifgf_shard_pack(self._h, int(level), int(nrhs), _ptr(ids), int(ids.numel()), _ptr(dst),
+                                         _stream(stream)))
+
+    def unpack(self, level: int, nrhs: int, src, first: int, n: int, stream=None):
+        """Needed cones first .. first + n - 1 of the level <- the n blocks at src."""
+        _check(self._lib.ifgf_shard_unpack(self._h, int(level), int(nrhs), _ptr(src), int(first), int(n),
+                                           _stream(stream)))
+
+    def near_leaf(self, dens_sorted, out_sorted, nrhs: int, stream=None):
+        _check(self._lib.ifgf_shard_near_leaf(self._h, _ptr(dens_sorted), int(nrhs), _ptr(out_sorted),
+                                              _stream(stream)))
+
+    def level(self, level: int, out_sorted, nrhs: int, stream=None):
+        _check(self._lib.ifgf_shard_level(self._h, int(level), int(nrhs), _ptr(out_sorted), _stream(stream)))
+
+    def destroy(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _check(self._lib.ifgf_shard_destroy(h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def measure_peaks() -> dict:
@@ -266,6 +377,17 @@ class Plan:
         _check(self._lib.ifgf_plan_query(self._h, int(what), int(level),
                                          buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(cnt2)))
         return buf[: cnt.value]
+
+    def permute(self, src, dst, to_sorted: bool, nrhs: int | None = None, stream=None):
+        """dst <- src reordered between the caller's point order and the sorted order (ifgf_permute)."""
+        n = int(src.shape[0]) if nrhs is None else int(nrhs)
+        _check(self._lib.ifgf_permute(self._h, _ptr(src), n, _ptr(dst), 1 if to_sorted else 0, _stream(stream)))
+        return dst
+
+    def debug_drop_cone(self, level: int, cone: int) -> None:
+        """Fault injection for tests: every lookup of relevant cone `cone` of `level` misses from now
+        on (ifgf_debug_drop_cone); the next apply records IFGF_ERR_INTERNAL in status()."""
+        _check(self._lib.ifgf_debug_drop_cone(self._h, int(level), int(cone)))
 
     def status(self) -> int:
         return int(self.query(Q.STATUS)[0])

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, f"libifgf_{platform.machine()}.so")
-SOURCES = ["util.cu", "plan.cu", "apply.cu", "api.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["util.cu", "plan.cu", "apply.cu", "api.cu", "noalloc.cu", "batch.cu", "shard.cu"]
 # throughput probes for the roofline denominators (a library of their own)
 PEAKS_LIB = os.path.join(BUILD, f"libifgf_peaks_{platform.machine()}.so")
 PEAKS_SOURCES = ["peaks.cu"]

@@ -570,6 +570,45 @@ const char* ifgf_last_error(void) { return t_last_error.c_str(); }
 
 int64_t ifgf_launch_count(void) { return g_launches.load(); }
 
+void ifgf_debug_fail_allocation(int64_t n) { g_fail_alloc_in.store(n > 0 ? n : 0); }
+
+ifgf_status ifgf_permute(ifgf_plan plan, const void* in, int32_t nrhs, void* out, int32_t to_sorted, void* stream) {
+    if (!plan || !in || !out || in == out || nrhs < 1) {
+        set_last_error("permute: NULL or aliased buffers, or nrhs < 1");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    return guard([&] {
+        IFGF_CUDA(cudaSetDevice(plan->device));
+        permute_points(*plan, in, nrhs, out, to_sorted != 0, (cudaStream_t)stream);
+    });
+}
+
+ifgf_status ifgf_debug_drop_cone(ifgf_plan plan, int32_t level, int64_t cone) {
+    if (!plan) {
+        set_last_error("NULL plan");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    Plan& p = *plan;
+    if (level < 3 || level > p.D || cone < 0 || cone >= p.L[level].nc) {
+        set_last_error("level or cone out of range");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    Level& L = p.L[level];
+    if (!L.slot) {
+        set_last_error("the level keeps sorted cone lists, not a dense table");
+        return IFGF_ERR_UNSUPPORTED;
+    }
+    return guard([&] {
+        IFGF_CUDA(cudaSetDevice(p.device));
+        IFGF_CUDA(cudaDeviceSynchronize());
+        int32_t box = 0, gam = 0;
+        IFGF_CUDA(cudaMemcpy(&box, L.cone_box + cone, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        IFGF_CUDA(cudaMemcpy(&gam, L.cone_gam + cone, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        const int32_t none = -1;
+        IFGF_CUDA(cudaMemcpy(L.slot + (int64_t)box * L.g.C + gam, &none, sizeof(int32_t), cudaMemcpyHostToDevice));
+    });
+}
+
 void ifgf_timing_enable(int32_t on) {
     TimingState& t = timing();
     std::lock_guard<std::mutex> lk(t.mu);

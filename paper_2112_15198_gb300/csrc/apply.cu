@@ -48,10 +48,10 @@ constexpr int kNearTile = 128;
 __global__ void __launch_bounds__(kNearThreads)
 k_near_tile_f32(const int4* __restrict__ kD, const int32_t* __restrict__ startD, const int32_t* __restrict__ nnb,
                 const int32_t* __restrict__ nb, const float4* __restrict__ off, const float2* __restrict__ as,
-                float2* __restrict__ Is, int64_t N, float ku, float inv4piu) {
+                float2* __restrict__ Is, int64_t N, float ku, float inv4piu, int l0) {
     __shared__ float4 s_p[kNearTile];  // source position in the target box's grid frame; w = source index
     __shared__ float2 s_a[kNearTile];
-    const int l = blockIdx.x;
+    const int l = l0 + blockIdx.x;  // leaf boxes [l0, l0 + gridDim.x)
     const int64_t r = blockIdx.y;
     const int tid = threadIdx.x;
     const int t0 = startD[l], m = startD[l + 1] - t0;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kLeafThreads)
 k_leaf_box_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ cone_gam, LevelGrid g,
                const int32_t* __restrict__ startD, const float4* __restrict__ off, const float2* __restrict__ as,
                int64_t N, float kh, float hinv, const float* __restrict__ W, float2* __restrict__ coef, int cstride,
-               int nrhs) {
+               int nrhs, int b0, int c_lo, int c_hi) {
     constexpr int P = PS * PT * PP;
     constexpr int NW = kLeafThreads / 32;
     constexpr int NCP = P <= 75 ? kLeafCones : 8;  // cones per pass (shared memory below 48 KB)
@@ -209,10 +209,12 @@ k_leaf_box_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ cone
     __shared__ float2 s_a[kLeafSrc];
     __shared__ float2 f[NCP][P];
     __shared__ float2 tmp[NW][P];
-    const int b = blockIdx.x;
+    // leaf boxes [b0, b0 + gridDim.x); only the cones [c_lo, c_hi) are evaluated, cone c is written
+    // at block c - c_lo of coef
+    const int b = b0 + blockIdx.x;
     const int r = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int c0 = bcs[b], c1 = bcs[b + 1];
+    const int c0 = max(bcs[b], c_lo), c1 = min(bcs[b + 1], c_hi);
     if (c0 == c1) return;
     const int j0 = startD[b], j1 = startD[b + 1];
     const float2* ar = as + (int64_t)r * N;
@@ -297,7 +299,7 @@ k_leaf_box_f32(const int32_t* __restrict__ bcs, const int32_t* __restrict__ cone
                     a.x = fmaf(w, v.x, a.x);
                     a.y = fmaf(w, v.y, a.y);
                 }
-                coef[((int64_t)(cc + cl) * nrhs + r) * cstride + n] = a;
+                coef[((int64_t)(cc + cl - c_lo) * nrhs + r) * cstride + n] = a;
             }
             __syncwarp();
         }
@@ -761,9 +763,10 @@ __global__ void __launch_bounds__(kThreads, NR == 1 ? 5 : 4) k_interp_f32(int64_
                              const int32_t* __restrict__ cs, const float4* __restrict__ off,
                              ConeMap cm, LevelGrid g, const float2* __restrict__ coef,
                              const float* __restrict__ phtab, float ku, float inv4piu, float2* __restrict__ Is,
-                             int cstride, int nrhs, int* __restrict__ status) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+                             int cstride, int nrhs, int* __restrict__ status, int64_t i0, int64_t i1) {
+    // targets [i0, i1) of the sorted points; Is is [nrhs][N]
+    const int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= i1) return;
     const int r0 = blockIdx.y * NR;
     const int nv = min(NR, nrhs - r0);
     const int A = pbox_d[i];
@@ -1717,29 +1720,37 @@ void for_each_slice(const Plan& p, int d, F&& launch) {
     }
 }
 
-// Interpolation to the targets of level d for nrhs value sets: one set per thread for a single
-// set, else two or four sets per thread sharing the geometry.
+// Interpolation to the targets [i0, i1) of level d for nrhs value sets, from the coefficients c
+// found through cm: one set per thread for a single set, else two or four sets per thread sharing
+// the geometry.
 template <int PS, int PT, int PP>
-void launch_interp_f32(Plan& p, int d, int nrhs, float2* Is, cudaStream_t s) {
+void launch_interp_f32(Plan& p, int d, int nrhs, float2* Is, cudaStream_t s, ConeMap cm, const float2* c, int64_t i0,
+                       int64_t i1) {
     const int64_t N = p.N;
     Level& L = p.L[d];
     Level& LD = p.L[p.D];
     const int sh = p.D - d;
     const float ku = (float)(p.kappa * p.u);
     const float inv4piu = (float)(1.0 / (4.0 * M_PI * p.u));
-    const float2* c = (const float2*)level_coef(p, d, nrhs);
-    const unsigned gx = grid_for(N, kThreads);
+    const unsigned gx = grid_for(i1 - i0, kThreads);
+    if (i1 <= i0) return;
     if (nrhs == 1)
         IFGF_LAUNCH((k_interp_f32<PS, PT, PP, 1>), dim3(gx, 1), kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k,
-                    L.ncs, L.cs, p.off, L.cmap(), L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status);
+                    L.ncs, L.cs, p.off, cm, L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status, i0, i1);
     else if (nrhs <= 3)
         IFGF_LAUNCH((k_interp_f32<PS, PT, PP, 2>), dim3(gx, (nrhs + 1) / 2), kThreads, 0, s, N, sh, L.pbox, LD.pbox,
-                    LD.k, L.k, L.ncs, L.cs, p.off, L.cmap(), L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs,
-                    p.d_status);
+                    LD.k, L.k, L.ncs, L.cs, p.off, cm, L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status, i0,
+                    i1);
     else
         IFGF_LAUNCH((k_interp_f32<PS, PT, PP, 4>), dim3(gx, (nrhs + 3) / 4), kThreads, 0, s, N, sh, L.pbox, LD.pbox,
-                    LD.k, L.k, L.ncs, L.cs, p.off, L.cmap(), L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs,
-                    p.d_status);
+                    LD.k, L.k, L.ncs, L.cs, p.off, cm, L.g, c, L.phtab, ku, inv4piu, Is, p.cstride, nrhs, p.d_status, i0,
+                    i1);
+}
+
+// Interpolation to every target of level d from the level's coefficients.
+template <int PS, int PT, int PP>
+void launch_interp_f32(Plan& p, int d, int nrhs, float2* Is, cudaStream_t s) {
+    launch_interp_f32<PS, PT, PP>(p, d, nrhs, Is, s, p.L[d].cmap(), (const float2*)level_coef(p, d, nrhs), 0, p.N);
 }
 
 // Levels D..3 of the many-density path: interpolation to the targets of level d (Algorithm 8),
@@ -1834,16 +1845,46 @@ void run_apply_multi(Plan& p, const void* dens, int nrhs, void* out, cudaStream_
     }
 }
 
+// Propagation of the parent cones [lo, lo + n) of level d-1 (mixed precision, nrhs <= 3 value
+// sets): child coefficients cc found through cm (level d), parent coefficients written from cp
+// on (parent cone lo at cp); node tables where level d-1 has them.
+template <int PS, int PT, int PP>
+void launch_prop_f32(Plan& p, int d, int nrhs, int64_t lo, int64_t n, ConeMap cm, const float2* cc, float2* cp,
+                     cudaStream_t s) {
+    Level& L = p.L[d];
+    Level& Lp = p.L[d - 1];
+    const int sh = p.D - d;
+    const float ku = (float)(p.kappa * p.u);
+    if (n <= 0) return;
+    if (Lp.n_gam > 0 && PS * PT * PP <= 75) {  // tables are built for (3,5,5) only
+        TimedScope ts_(TK_PROP, s);
+        constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
+                      TP = PS * PT * PP <= 75 ? PP : 5;
+        const dim3 grid((unsigned)((n + kWarpCones - 1) / kWarpCones), 1);
+        if (nrhs == 1)
+            IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP, 1>), grid, 32 * kWarpCones, 0, s, n, Lp.cone_box + lo,
+                        Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, cm, Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list,
+                        Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, cc, cp, p.Wf, p.cstride, nrhs, p.d_status);
+        else
+            IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP, 0>), grid, 32 * kWarpCones, 0, s, n, Lp.cone_box + lo,
+                        Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, cm, Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list,
+                        Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, cc, cp, p.Wf, p.cstride, nrhs, p.d_status);
+    } else {
+        TimedScope ts_(TK_PROP_GEN, s);
+        IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((n + kPropCones - 1) / kPropCones), nrhs), kPropThreads,
+                    0, s, n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, cm, L.g, cc, cp, sh, ku,
+                    p.Wf, p.cstride, nrhs, p.d_status);
+    }
+}
+
 // Levels D..3 of the mixed path with few densities: interpolation to the targets of level d
 // (Algorithm 8), then propagation into level d-1 (Algorithm 7), from node tables where the
 // level has them.
 template <int PS, int PT, int PP>
 void sweep_levels_f32(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mask) {
     const int D = p.D;
-    const float ku = (float)(p.kappa * p.u);
     for (int d = D; d >= 3; --d) {
         Level& L = p.L[d];
-        const int sh = D - d;
         if ((mask >> d) & 1) {
             TimedScope ts_(TK_INTERP, s);
             launch_interp_f32<PS, PT, PP>(p, d, nrhs, Is, s);
@@ -1853,31 +1894,10 @@ void sweep_levels_f32(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mas
         const float2* cc = (const float2*)level_coef(p, d, nrhs);
         float2* cp = (float2*)level_coef(p, d - 1, nrhs);
         const int64_t cone = (int64_t)nrhs * p.cstride;
-        if (Lp.nc > 0 && Lp.n_gam > 0 && PS * PT * PP <= 75) {  // tables are built for (3,5,5) only
-            TimedScope ts_(TK_PROP, s);
-            constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
-                          TP = PS * PT * PP <= 75 ? PP : 5;
+        if (Lp.nc > 0)
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                const dim3 grid((unsigned)((n + kWarpCones - 1) / kWarpCones), 1);
-                if (nrhs == 1)
-                    IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP, 1>), grid, 32 * kWarpCones, 0, s, n, Lp.cone_box + lo,
-                                Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k,
-                                Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, cc, cp + lo * cone, p.Wf,
-                                p.cstride, nrhs, p.d_status);
-                else
-                    IFGF_LAUNCH((k_prop_warp_f32<TS, TT, TP, 0>), grid, 32 * kWarpCones, 0, s, n, Lp.cone_box + lo,
-                                Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k,
-                                Lp.tab_list, Lp.tab_perm, Lp.tab_nseg, Lp.tab_seg, cc, cp + lo * cone, p.Wf,
-                                p.cstride, nrhs, p.d_status);
+                launch_prop_f32<PS, PT, PP>(p, d, nrhs, lo, n, L.cmap(), cc, cp + lo * cone, s);
             });
-        } else if (Lp.nc > 0) {
-            TimedScope ts_(TK_PROP_GEN, s);
-            for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                IFGF_LAUNCH((k_prop_f32<PS, PT, PP>), dim3((unsigned)((n + kPropCones - 1) / kPropCones), nrhs),
-                            kPropThreads, 0, s, n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k,
-                            L.cmap(), L.g, cc, cp + lo * cone, sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
-            });
-        }
     }
 }
 
@@ -1959,7 +1979,7 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
             {
                 TimedScope ts_(TK_NEAR, s);
                 IFGF_LAUNCH(k_near_tile_f32, dim3((unsigned)LD.n, nrhs), kNearThreads, 0, s, LD.k, LD.start, LD.nnb,
-                            LD.nb, p.off, as, Is, N, ku, inv4piu);
+                            LD.nb, p.off, as, Is, N, ku, inv4piu, 0);
             }
         else
             IFGF_CUDA(cudaMemsetAsync(Is, 0, sizeof(float2) * N * nrhs, s));
@@ -1969,7 +1989,7 @@ void run_apply(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, b
                 TimedScope ts_(TK_LEAF, s);
                 IFGF_LAUNCH((k_leaf_box_f32<PS, PT, PP>), dim3((unsigned)LD.n, nrhs), kLeafThreads, 0, s, LD.bcs,
                             LD.cone_gam, LD.g, LD.start, p.off, as, N, kh, 1.0f / LD.g.hg, p.Wf,
-                            (float2*)level_coef(p, D, nrhs), p.cstride, nrhs);
+                            (float2*)level_coef(p, D, nrhs), p.cstride, nrhs, 0, 0, (int)LD.nc);
             }
         sweep_levels_f32<PS, PT, PP>(p, nrhs, Is, s, mask);
         {
@@ -2104,6 +2124,70 @@ void run_apply_stokes(Plan& p, const float* forces, int nf, float* vel, const Te
 }
 
 }  // namespace
+
+// ---- steps of one rank of a distributed apply (Sec. 3.2), mixed precision, nrhs <= 3 ------------
+namespace {
+template <int PS, int PT, int PP>
+void shard_near_leaf_t(Plan& p, const float2* as, int nrhs, float2* Is, int64_t b0, int64_t b1, int64_t lb0,
+                       int64_t lb1, int64_t c_lo, int64_t c_hi, float2* coefD, cudaStream_t s) {
+    const int64_t N = p.N;
+    Level& LD = p.L[p.D];
+    const float ku = (float)(p.kappa * p.u);
+    const float inv4piu = (float)(1.0 / (4.0 * M_PI * p.u));
+    if (b1 > b0) {
+        TimedScope ts_(TK_NEAR, s);
+        IFGF_LAUNCH(k_near_tile_f32, dim3((unsigned)(b1 - b0), nrhs), kNearThreads, 0, s, LD.k, LD.start, LD.nnb, LD.nb,
+                    p.off, as, Is, N, ku, inv4piu, (int)b0);
+    }
+    if (c_hi > c_lo) {
+        TimedScope ts_(TK_LEAF, s);
+        IFGF_LAUNCH((k_leaf_box_f32<PS, PT, PP>), dim3((unsigned)(lb1 - lb0), nrhs), kLeafThreads, 0, s, LD.bcs,
+                    LD.cone_gam, LD.g, LD.start, p.off, as, N, (float)(p.kappa * LD.g.h64), 1.0f / LD.g.hg, p.Wf, coefD,
+                    p.cstride, nrhs, (int)lb0, (int)c_lo, (int)c_hi);
+    }
+}
+}  // namespace
+
+void shard_near_leaf(Plan& p, const float2* as, int nrhs, float2* Is, int64_t b0, int64_t b1, int64_t lb0, int64_t lb1,
+                     int64_t c_lo, int64_t c_hi, float2* coefD, cudaStream_t s) {
+    if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
+        shard_near_leaf_t<3, 5, 5>(p, as, nrhs, Is, b0, b1, lb0, lb1, c_lo, c_hi, coefD, s);
+    else
+        shard_near_leaf_t<5, 7, 7>(p, as, nrhs, Is, b0, b1, lb0, lb1, c_lo, c_hi, coefD, s);
+}
+
+void shard_interp(Plan& p, int d, int nrhs, float2* Is, const ConeMap& cm, const float2* coef, int64_t i0, int64_t i1,
+                  cudaStream_t s) {
+    TimedScope ts_(TK_INTERP, s);
+    if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
+        launch_interp_f32<3, 5, 5>(p, d, nrhs, Is, s, cm, coef, i0, i1);
+    else
+        launch_interp_f32<5, 7, 7>(p, d, nrhs, Is, s, cm, coef, i0, i1);
+}
+
+void shard_prop(Plan& p, int d, int nrhs, int64_t lo, int64_t hi, const ConeMap& cm, const float2* cc, float2* cp,
+                cudaStream_t s) {
+    if (p.Ps == 3 && p.Pt == 5 && p.Pp == 5)
+        launch_prop_f32<3, 5, 5>(p, d, nrhs, lo, hi - lo, cm, cc, cp, s);
+    else
+        launch_prop_f32<5, 7, 7>(p, d, nrhs, lo, hi - lo, cm, cc, cp, s);
+}
+
+void permute_points(Plan& p, const void* in, int nrhs, void* out, bool to_sorted, cudaStream_t s) {
+    const dim3 gN(grid_for(p.N, kThreads), nrhs);
+    TimedScope ts_(TK_PERM, s);
+    if (p.precision == IFGF_PREC_MIXED) {
+        if (to_sorted)
+            IFGF_LAUNCH(k_perm_in<float2>, gN, kThreads, 0, s, (const float2*)in, p.perm, p.N, (float2*)out);
+        else
+            IFGF_LAUNCH(k_perm_out<float2>, gN, kThreads, 0, s, (const float2*)in, p.perm, p.N, (float2*)out);
+    } else {
+        if (to_sorted)
+            IFGF_LAUNCH(k_perm_in<double2>, gN, kThreads, 0, s, (const double2*)in, p.perm, p.N, (double2*)out);
+        else
+            IFGF_LAUNCH(k_perm_out<double2>, gN, kThreads, 0, s, (const double2*)in, p.perm, p.N, (double2*)out);
+    }
+}
 
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask) {
     // densities in blocks of at most rhs_block, one level sweep per block

@@ -30,6 +30,9 @@ constexpr int kMaxCous = 189;  // |M B| <= 189 (Sec. 3.3)
 constexpr int kMaxOrder = 8;
 
 extern std::atomic<int64_t> g_launches;
+// Fault injection for tests (ifgf_debug_fail_allocation): when positive, the device allocation
+// that brings it to zero fails as if the device were out of memory.
+extern std::atomic<int64_t> g_fail_alloc_in;
 
 // Per-level cone grid: counts, exact-classification tables and interpolation-node tables.
 struct LevelGrid {
@@ -37,6 +40,7 @@ struct LevelGrid {
     float hg;                  // circumradius h_d in grid units
     float s_scale, t_scale, p_scale;  // ns/eta, nt/pi, np/(2 pi): candidate bins
     float s2w, t2w, p2w;       // 2/ds, 2/dt, 2/dp: local coordinate scales
+    float ms, tA, tB, mp;      // edge margins of the classification's fast path (bin widths)
     double ds64, dt64, dp64;   // interval widths
     double h64;                // circumradius in physical units
     const float* R2;           // [ns]  (h/(i ds))^2, grid units
@@ -58,15 +62,34 @@ struct LevelGrid {
 // Cone lookup (box, gamma) -> index of the relevant cone, or -1. Dense levels keep the table
 // slot[box * C + gamma] (one load); levels whose table would be too large keep only the
 // cone list, sorted by (box, gamma), with the first cone of every box (binary search).
+// Sparse levels may also keep rows[box * nrow + w] = the first cone of the box whose gamma is at
+// least w * np (w = is * nt + it, one row per (s, theta) bin, the next box's first row closing
+// the last), so that a search covers the few relevant cones of one phi-row instead of the box.
 struct ConeMap {
     const int32_t* slot;  // dense table, or nullptr
     int32_t C;
     const int32_t* bcs;   // [n+1] first cone of every box (sparse levels)
     const int32_t* gam;   // [nc] cone index gamma of every cone (sparse levels)
+    const int32_t* rows;  // [n * nrow + 1] row starts (sparse levels), or nullptr
+    int32_t nrow, np;     // rows per box (ns * nt) and the phi count
+    // A rank of a distributed apply holds some of the level's cones: g2l maps a cone's index in the
+    // level's list to its block in the rank's buffer, -1 when the rank does not hold it.
+    const int32_t* g2l = nullptr;
     __device__ __forceinline__ int find(int box, int gamma) const {
+        const int s = find_global(box, gamma);
+        return (g2l && s >= 0) ? __ldg(&g2l[s]) : s;
+    }
+    __device__ __forceinline__ int find_global(int box, int gamma) const {
         if (slot) return __ldg(&slot[(int64_t)box * C + gamma]);
-        int lo = __ldg(&bcs[box]);
-        const int end = __ldg(&bcs[box + 1]);
+        int lo, end;
+        if (rows) {
+            const int64_t w = (int64_t)box * nrow + gamma / np;
+            lo = __ldg(&rows[w]);
+            end = __ldg(&rows[w + 1]);
+        } else {
+            lo = __ldg(&bcs[box]);
+            end = __ldg(&bcs[box + 1]);
+        }
         int hi = end;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -93,7 +116,8 @@ struct Level {
     int64_t nc = 0;                // relevant cones R_C^d
     int32_t* slot = nullptr;       // [n*C] cone index or -1 (dense levels; nullptr when sparse)
     int32_t* bcs = nullptr;        // [n+1] first cone of every box (sparse levels)
-    ConeMap cmap() const { return ConeMap{slot, g.C, bcs, cone_gam}; }
+    int32_t* rows = nullptr;       // [n * ns * nt + 1] row starts of the cone list (sparse levels)
+    ConeMap cmap() const { return ConeMap{slot, g.C, bcs, cone_gam, rows, g.ns * g.nt, g.np}; }
     int32_t* cone_box = nullptr;   // [nc]
     int32_t* cone_gam = nullptr;   // [nc]
     float* phtab = nullptr;        // [28] (kappa H_d sqrt(m)) mod 2 pi, m = |k_A - k_B|^2
@@ -184,6 +208,8 @@ T* dalloc(Plan& p, size_t count) {
     void* ptr = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
+    if (g_fail_alloc_in.load(std::memory_order_relaxed) > 0 && g_fail_alloc_in.fetch_sub(1) == 1)
+        fail(IFGF_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)");
     cudaMemPool_t pool = device_pool(p.device);
     cudaError_t e = cudaMallocFromPoolAsync(&ptr, bytes, pool, p.stream);
     if (e != cudaSuccess) {  // return the pool's cached memory to the device and try once more
@@ -265,6 +291,19 @@ inline char* level_coef(const Plan& p, int d, int nb) {
     return ((p.D - d) % 2 == 0) ? p.arena : p.arena + (size_t)(p.arena_cones - p.L[d].nc) * cone;
 }
 void destroy_plan(Plan& p);
+// Steps of one rank of a distributed apply (apply.cu; mixed precision, at most 3 value sets):
+// near field of the leaf boxes [b0, b1) and LevelDEvaluations of the level-D cones [c_lo, c_hi)
+// (whose boxes are [lb0, lb1)), written at coefD; Interpolation(d) of the targets [i0, i1); and
+// Propagation(d) of the level-(d-1) cones [lo, hi), parent cone lo written at cp.  Sorted
+// densities as and results Is are [nrhs][N]; cone lookups go through cm (with the rank's map).
+void shard_near_leaf(Plan& p, const float2* as, int nrhs, float2* Is, int64_t b0, int64_t b1, int64_t lb0, int64_t lb1,
+                     int64_t c_lo, int64_t c_hi, float2* coefD, cudaStream_t s);
+void shard_interp(Plan& p, int d, int nrhs, float2* Is, const ConeMap& cm, const float2* coef, int64_t i0, int64_t i1,
+                  cudaStream_t s);
+void shard_prop(Plan& p, int d, int nrhs, int64_t lo, int64_t hi, const ConeMap& cm, const float2* cc, float2* cp,
+                cudaStream_t s);
+// Caller order <-> sorted order of [nrhs][N] complex vectors of the plan's precision.
+void permute_points(Plan& p, const void* in, int nrhs, void* out, bool to_sorted, cudaStream_t s);
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask);
 // Green tensor c (alpha delta_ij / r + r_i r_j / r^3): the Stokeslet (c = 1/(8 pi mu), alpha = 1)
 // or Kelvin's solution of linear elasticity (c = 1/(16 pi mu (1 - nu)), alpha = 3 - 4 nu).
@@ -325,6 +364,26 @@ __device__ __forceinline__ void classify_exact(const LevelGrid& g, float vx, flo
     while (ip + 1 < g.np && GE(ip + 1)) ++ip;
 }
 
+// Fast path of the exact classification.  (fs, ft, fp) are the approximate bin coordinates
+// s ns/eta, theta nt/pi, phi np/(2 pi) of the offset v, (is, it, ip) their integer parts.  The
+// approximate coordinates differ from the true ones by a few 1e-7 (relative for s, radians for the
+// angles), and each exact edge test decides as the true geometry does unless the point lies within
+// a few 1e-7 of the edge (for theta, within about 1.5e-7 / tan(theta_i) of edge i, which grows
+// near the poles).  Where every coordinate lies inside its candidate bin by more than the level's
+// margins (about eight times those bounds), the candidate bins are the exact ones; the polar theta
+// bins, points on the axis and points beyond the grid take the exact tests.
+__device__ __forceinline__ bool bins_certain(const LevelGrid& g, float vx, float vy, float fs, float ft, float fp,
+                                             int is, int it, int ip) {
+    if ((unsigned)is >= (unsigned)g.ns || (unsigned)ip >= (unsigned)g.np) return false;
+    const int k = min(it, g.nt - 1 - it);  // bins between this one and the nearest polar bin
+    if (k <= 0 || (vx == 0.0f && vy == 0.0f)) return false;
+    const float es = fs - (float)is, et = ft - (float)it, ep = fp - (float)ip;
+    const float ms = g.ms * (float)(is + 1);
+    const float mt = g.tA + __fdividef(g.tB, (float)k);
+    const bool s_ok = (is == 0 || es > ms) && (is == g.ns - 1 || es < 1.0f - ms);
+    return s_ok && et > mt && et < 1.0f - mt && ep > g.mp && ep < 1.0f - g.mp;
+}
+
 // atan2 for evaluation coordinates: octant symmetry reduces the argument to t in [0, 1], where
 // atan(t) = t P(t^2) with an odd polynomial of degree 15 fitted to atan by iteratively
 // reweighted least squares on Chebyshev nodes (near-minimax); max error 1.4e-7 rad in FP32.
@@ -366,10 +425,11 @@ __device__ __forceinline__ ConeLocal locate_f32(const LevelGrid& g, float vx, fl
     float ph = fast_atan2(vy, vx);
     if (ph < 0.0f) ph += 6.28318530717958647692f;
     ConeLocal o;
-    o.is = (int)(s * g.s_scale);
-    o.it = (int)(th * g.t_scale);
-    o.ip = (int)(ph * g.p_scale);
-    classify_exact(g, vx, vy, vz, r2, o.is, o.it, o.ip);
+    const float fs = s * g.s_scale, ft = th * g.t_scale, fp = ph * g.p_scale;
+    o.is = (int)fs;
+    o.it = (int)ft;
+    o.ip = (int)fp;
+    if (!bins_certain(g, vx, vy, fs, ft, fp, o.is, o.it, o.ip)) classify_exact(g, vx, vy, vz, r2, o.is, o.it, o.ip);
     o.r = r2 * rinv;
     o.ts = fmaf(s, g.s2w, -(float)(2 * o.is + 1));
     o.tt = fmaf(th, g.t2w, -(float)(2 * o.it + 1));
@@ -389,8 +449,9 @@ __device__ __forceinline__ int classify_f32(const LevelGrid& g, float vx, float 
     const float rxy = rxy2 > 0.0f ? rxy2 * rsqrtf(rxy2) : 0.0f;
     float ph = fast_atan2(vy, vx);
     if (ph < 0.0f) ph += 6.28318530717958647692f;
-    int is = (int)(s * g.s_scale), it = (int)(fast_atan2(rxy, vz) * g.t_scale), ip = (int)(ph * g.p_scale);
-    classify_exact(g, vx, vy, vz, r2, is, it, ip);
+    const float fs = s * g.s_scale, ft = fast_atan2(rxy, vz) * g.t_scale, fp = ph * g.p_scale;
+    int is = (int)fs, it = (int)ft, ip = (int)fp;
+    if (!bins_certain(g, vx, vy, fs, ft, fp, is, it, ip)) classify_exact(g, vx, vy, vz, r2, is, it, ip);
     return (is * g.nt + it) * g.np + ip;
 }
 

@@ -533,7 +533,34 @@ k_mark_parent_nodes_chunk(const int32_t* __restrict__ gchunk, const int32_t* __r
     for (int ch = 0; ch < nch; ++ch) {
         const int4 kk = kd[k0 + ch];
         const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
-        for (int n = lane; n < P; n += 32) mark.mark(k0 + ch, s_alpha[o][n]);
+        // the 75 nodes fall in a few child cones: collect the distinct ones over all nodes (lane g
+        // keeps the g-th), then mark each once
+        int a[3];
+        bool pend[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int n = lane + 32 * j;
+            pend[j] = n < P;
+            a[j] = pend[j] ? s_alpha[o][n] : -1;
+        }
+        int mine = -1, G = 0;
+        for (int guard = 0; guard < P; ++guard) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, pend[0]), b1 = __ballot_sync(0xffffffffu, pend[1]),
+                           b2 = __ballot_sync(0xffffffffu, pend[2]);
+            if (!(b0 | b1 | b2)) break;
+            const int sj = b0 ? 0 : (b1 ? 1 : 2);
+            const int src = __ffs(b0 ? b0 : (b1 ? b1 : b2)) - 1;
+            const int v = __shfl_sync(0xffffffffu, sj == 0 ? a[0] : (sj == 1 ? a[1] : a[2]), src);
+            if (lane == (G & 31)) mine = v;
+            if ((G & 31) == 31) {  // 32 distinct cones collected: mark them before collecting more
+                mark.mark(k0 + ch, mine);
+                mine = -1;
+            }
+            ++G;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) pend[j] = pend[j] && a[j] != v;
+        }
+        if (mine >= 0) mark.mark(k0 + ch, mine);
     }
 }
 
@@ -593,6 +620,28 @@ __global__ void k_box_cone_starts(int n, int64_t nc, const int32_t* __restrict__
     bcs[b] = (int32_t)lo;
 }
 
+// Row starts of a sparse level's cone list: entry b * nrow + w is the first cone of box b with
+// gamma >= w * np; entry n * nrow closes the last row.
+__global__ void k_row_starts(int64_t total, int nrow, int np, const int32_t* __restrict__ bcs,
+                             const int32_t* __restrict__ cone_gam, int32_t* __restrict__ rows) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > total) return;
+    const int64_t b = e / nrow;
+    const int w = (int)(e - b * nrow);
+    if (e == total) {
+        rows[e] = bcs[b];  // b == n: one past the last cone
+        return;
+    }
+    int lo = bcs[b], hi = bcs[b + 1];
+    const int key = w * np;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cone_gam[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    rows[e] = lo;
+}
+
 __global__ void k_finalize_cones(int32_t* __restrict__ slot, const int32_t* __restrict__ pos, int64_t total, int C,
                                  int32_t* __restrict__ cone_box, int32_t* __restrict__ cone_gam) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -640,6 +689,13 @@ void build_grid(Plan& p, int d, const ifgf_options& opt, std::vector<std::vector
     g.s_scale = (float)(ns / eta);
     g.t_scale = (float)(nt / M_PI);
     g.p_scale = (float)(np / (2.0 * M_PI));
+    // Margins (in bin widths) of the classification's fast path: farther from every edge of its
+    // candidate bin than these, a point provably has the bins that the exact edge tests give
+    // (bounds of the approximate coordinates and of the tests' rounding, times about eight).
+    g.ms = 4e-6f;                                        // s: relative, times (bin + 1)
+    g.tA = (float)(4e-6 * nt / M_PI);                    // theta: approximation error
+    g.tB = (float)(1.2e-6 * (double)nt * nt / (2.0 * M_PI));  // theta: edge test near the poles
+    g.mp = (float)(8e-6 * np / (2.0 * M_PI));            // phi
     g.s2w = (float)(2.0 / g.ds64);
     g.t2w = (float)(2.0 / g.dt64);
     g.p2w = (float)(2.0 / g.dp64);
@@ -1027,6 +1083,14 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
             L.bcs = dalloc<int32_t>(p, (size_t)L.n + 1);
             IFGF_LAUNCH(k_box_cone_starts, grid_for((int64_t)L.n + 1, kThreads), kThreads, 0, s, L.n, L.nc, L.cone_box,
                         L.bcs);
+            // row index of the sorted list while it stays within a memory budget (4 bytes per row)
+            const int64_t nrow = (int64_t)L.g.ns * L.g.nt;
+            const int64_t rtotal = (int64_t)L.n * nrow;
+            if (rtotal < ((int64_t)1 << 31) && rtotal * 4 <= ((int64_t)1 << 30)) {
+                L.rows = dalloc<int32_t>(p, (size_t)rtotal + 1);
+                IFGF_LAUNCH(k_row_starts, grid_for(rtotal + 1, kThreads), kThreads, 0, s, rtotal, (int)nrow, L.g.np,
+                            L.bcs, L.cone_gam, L.rows);
+            }
         }
         if (d < D && p.precision == IFGF_PREC_MIXED && p.Ps == 3 && p.Pt == 5 && p.Pp == 5) {
             build_node_tables(p, d);

@@ -7,6 +7,7 @@
 namespace ifgf {
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_fail_alloc_in{0};
 
 namespace {
 

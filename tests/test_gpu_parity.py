@@ -26,6 +26,45 @@ TREE_ITEMS = [
 ]
 
 
+def _dyadic_lattice(n=6000, seed=61):
+    """Points of the 1/128 lattice of the root cube near a sphere, so that many of them lie exactly
+    on box faces (the half-open rule of the root-cube reading decides their box) and on the
+    theta = pi/2, phi = j pi/4 and axis directions seen from box centres (the edge rules of the
+    classification decide their cone).  Two anchors at (0,0,0) and (1,1,1) fix the root cube:
+    H1 = 1 + 2^-20, a = -2^-21, and lattice point m sits at a + m H1 / 128, exactly."""
+    H1 = 1.0 + 2.0 ** -20
+    a = -(2.0 ** -21)
+    g = np.arange(129)
+    i, j, k = np.meshgrid(g, g, g, indexing="ij")
+    r = np.sqrt((i / 128 - 0.5) ** 2 + (j / 128 - 0.5) ** 2 + (k / 128 - 0.5) ** 2)
+    shell = np.abs(r - 0.4) < 0.5 / 128
+    m = np.stack([i[shell], j[shell], k[shell]])
+    rng = np.random.default_rng(seed)
+    m = m[:, rng.choice(m.shape[1], size=min(n, m.shape[1]), replace=False)]
+    pts = a + m.astype(np.float64) * H1 / 128.0
+    anchors = np.array([[0.0, 1.0], [0.0, 1.0], [0.0, 1.0]])
+    return np.ascontiguousarray(np.concatenate([anchors, pts], axis=1))
+
+
+def _stored(name):
+    """Targets and FP64 direct-sum values of a workload, from the values the oracle wrote
+    (tests/golden/make_direct_sums.py) when they match these inputs, else from the oracle now."""
+    import importlib.util
+    import os
+
+    spec = importlib.util.spec_from_file_location(
+        "make_direct_sums", os.path.join(os.path.dirname(__file__), "golden", "make_direct_sums.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    w = W.make(name)
+    pts, dens = w.points(), w.densities()
+    got = mk.load(name)
+    if got is not None and np.allclose(got[2], mk.input_check(pts, dens), rtol=1e-9, atol=1e-9):
+        return w, pts, dens, got[0], got[1]
+    tgt = w.targets()
+    return w, pts, dens, tgt, oracle.direct_sum(pts, w.kappa, dens, tgt)
+
+
 def _plan(pts, kappa, **kw):
     return ifgf.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(DEV), kappa, **kw)
 
@@ -83,6 +122,10 @@ CASES = {
     # (a, a, a/2) spheroid of the uneven batch: its leaf neighbour lists once came out truncated
     "batch_spheroid": lambda: (W.batch_problems(count=6, seed=17)[1].points(),
                                W.batch_problems(count=6, seed=17)[1].kappa, {}),
+    # the paper's third body, the prolate spheroid (a, a, 10a): long, thin, many levels
+    "prolate": lambda: (W.spheroid(20000, 0.05, 0.5, seed=51), 2 * math.pi * 8, {}),
+    # points exactly on box faces and on cone edges seen from box centres
+    "dyadic_lattice": lambda: (_dyadic_lattice(), 2 * math.pi * 4, {}),
 }
 
 
@@ -95,7 +138,7 @@ def test_tree_and_cones_bit_exact(case):
 
 
 @pytest.mark.parametrize("case", ["sphere4", "cloud_ragged", "spheroid", "two_points", "one_leaf_D3", "planar",
-                                  "deep", "laplace", "batch_spheroid"])
+                                  "deep", "laplace", "batch_spheroid", "prolate", "dyadic_lattice"])
 def test_fp64_matches_cpu_ifgf(case):
     pts, kappa, kw = CASES[case]()
     n = pts.shape[1]
@@ -108,7 +151,7 @@ def test_fp64_matches_cpu_ifgf(case):
 
 
 @pytest.mark.parametrize("case", ["sphere4", "cloud_ragged", "spheroid", "two_points", "one_leaf_D3", "planar",
-                                  "deep", "laplace", "batch_spheroid"])
+                                  "deep", "laplace", "batch_spheroid", "prolate", "dyadic_lattice"])
 def test_mixed_matches_cpu_ifgf(case):
     pts, kappa, kw = CASES[case]()
     n = pts.shape[1]
@@ -246,22 +289,33 @@ def test_nrhs_limit():
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_full_size_sphere64_sampled(prec):
-    """The 64-wavelength, 1,572,864-point sphere in the bench's configuration: error on 2,000
-    seeded targets against the direct sum, and the tree/cone lists against the oracle's."""
-    w = W.make("sphere64")
-    pts, kappa = w.points(), w.kappa
-    dens = w.densities()
-    tgt = w.targets()
-    exact = oracle.direct_sum(pts, kappa, dens, tgt)
-    gp = _plan(pts, kappa, precision=prec)
+    """The 64-wavelength, 1,572,864-point sphere: error on its 2,000 seeded targets against the
+    direct sum (measured 1.4e-4 in both precisions; bound about twice that), and the tree/cone
+    lists against the oracle's."""
+    w, pts, dens, tgt, exact = _stored("sphere64")
+    gp = _plan(pts, w.kappa, precision=prec)
     got = _apply(gp, dens, prec)[:, tgt]
     assert gp.status() == 0
     err = oracle.rel_l2(got, exact)
     print(f"sphere64 {prec}: rel. L2 error on {len(tgt)} targets = {err:.3e}")
-    assert err < 5e-4
+    assert err < 3e-4
     if prec == "mixed":
-        op = oracle.Plan(pts, kappa)
+        op = oracle.Plan(pts, w.kappa)
         assert_same_tree(gp, op)
+
+
+def test_full_size_prolate128_sampled():
+    """The prolate spheroid (a, a, 10a) of the paper's tests, 128 wavelengths long, N = 6,291,456:
+    error on 2,000 seeded targets against the direct sum, and the tree/cone lists against the
+    oracle's."""
+    w, pts, dens, tgt, exact = _stored("prolate128")
+    gp = _plan(pts, w.kappa, precision="mixed")
+    got = _apply(gp, dens, "mixed")[:, tgt]
+    assert gp.status() == 0
+    err = oracle.rel_l2(got, exact)
+    print(f"prolate128: D = {gp.D}, rel. L2 error on {len(tgt)} targets = {err:.3e}")
+    assert err < 3e-4
+    assert_same_tree(gp, oracle.Plan(pts, w.kappa))
 
 
 @pytest.mark.parametrize("nrhs", [4, 12, 32])
@@ -330,37 +384,30 @@ def test_sorted_cone_lists_equal_dense_tables(prec, nrhs):
         assert_same_tree(srt, oracle.Plan(pts, kappa))
 
 
-@pytest.mark.parametrize("name", ["sphere512", "sphere512_laplace"])
-def test_full_size_sphere512_sampled(name):
+@pytest.mark.parametrize("name,bound", [("sphere512", 1.5e-4), ("sphere512_laplace", 2e-4)])
+def test_full_size_sphere512_sampled(name, bound):
     """The 512-wavelength, 25,165,824-point sphere (sorted cone lists at the coarse levels) and its
-    Laplace repeat: error on 500 seeded targets against the direct sum."""
-    w = W.make(name)
-    pts, kappa = w.points(), w.kappa
-    dens = w.densities()
-    tgt = W.targets(w.n, 500, w.seed + 200)
-    gp = _plan(pts, kappa, precision="mixed")
+    Laplace repeat: error on 2,000 seeded targets against the direct sum, bounded at about twice
+    the measured error."""
+    w, pts, dens, tgt, exact = _stored(name)
+    gp = _plan(pts, w.kappa, precision="mixed")
     got = _apply(gp, dens, "mixed")[:, tgt]
     assert gp.status() == 0
-    exact = oracle.direct_sum(pts, kappa, dens, tgt)
     err = oracle.rel_l2(got, exact)
     print(f"{name}: D = {gp.D}, rel. L2 error on {len(tgt)} targets = {err:.3e}")
-    assert err < 5e-4
+    assert err < bound
 
 
 def test_full_size_oblate128_many_densities():
     """The 128-wavelength (a, a, a/4) spheroid, N = 6,291,456, 32 densities on the tensor-core path:
-    error of every density on 100 seeded targets against the direct sum."""
-    w = W.make("oblate128")
-    pts, kappa = w.points(), w.kappa
-    dens = w.densities()
-    tgt = W.targets(w.n, 100, w.seed + 200)
-    gp = _plan(pts, kappa, precision="mixed", max_nrhs=w.nrhs)
+    error of every density on 2,000 seeded targets against the direct sum."""
+    w, pts, dens, tgt, exact = _stored("oblate128")
+    gp = _plan(pts, w.kappa, precision="mixed", max_nrhs=w.nrhs)
     got = _apply(gp, dens, "mixed")[:, tgt]
     assert gp.status() == 0
-    exact = oracle.direct_sum(pts, kappa, dens, tgt)
-    worst = max(oracle.rel_l2(got[r], exact[r]) for r in range(w.nrhs))
-    print(f"oblate128 x 32: worst density rel. L2 error on {len(tgt)} targets = {worst:.3e}")
-    assert worst < 5e-4
+    errs = [oracle.rel_l2(got[r], exact[r]) for r in range(w.nrhs)]
+    print(f"oblate128 x 32: rel. L2 error on {len(tgt)} targets: mean {np.mean(errs):.3e}, worst {max(errs):.3e}")
+    assert max(errs) < 3e-4
 
 
 def test_cached_memory_is_reused_and_released():
