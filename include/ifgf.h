@@ -366,6 +366,20 @@ void ifgf_debug_fail_allocation(int64_t n);
 ifgf_status ifgf_debug_drop_cone(ifgf_plan plan, int32_t level, int64_t cone);
 
 /*
+ * Checked builds (compiled with -DIFGF_CHECKS; the Python binding loads one when IFGF_CHECKS=1):
+ * every cone lookup tests its box and the cone it returns, the interpolation tests every cousin
+ * box it reads, and ifgf_plan_create validates every index list of the plan (ranges, offsets,
+ * table segments) before returning; a failed test records IFGF_ERR_INTERNAL in the plan's status
+ * word (ifgf_plan_create returns it) and the access is skipped, so the device never traps.
+ * ifgf_checked_build returns 1 in such a build, 0 otherwise.
+ * ifgf_debug_corrupt_cousin(plan, level), in checked builds only, replaces the first cousin of the
+ * level's first box that has one by a box index past the level's boxes, so that the next apply's
+ * checks report it (IFGF_ERR_UNSUPPORTED in other builds, where it would be read out of bounds).
+ */
+int32_t ifgf_checked_build(void);
+ifgf_status ifgf_debug_corrupt_cousin(ifgf_plan plan, int32_t level);
+
+/*
  * Allocation-free Morton order of N points.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they need the order, because
  * their device memory is wholly owned by another allocator (a framework's caching pool or an

@@ -71,7 +71,8 @@ def load(build: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build else _build.LIB
+        checks = os.environ.get("IFGF_CHECKS", "0") == "1"  # the bounds-checked build
+        path = _build.build(checks=checks) if build else (_build.CHECKS_LIB if checks else _build.LIB)
         if not os.path.exists(path):
             raise RuntimeError(f"IFGF CUDA library not found at {path}; run __graft_entry__.build()")
         lib = ctypes.CDLL(path)
@@ -109,6 +110,10 @@ def load(build: bool = True):
         lib.ifgf_batch_apply.restype = ctypes.c_int
         lib.ifgf_batch_destroy.argtypes = [vp]
         lib.ifgf_batch_destroy.restype = ctypes.c_int
+        lib.ifgf_checked_build.argtypes = []
+        lib.ifgf_checked_build.restype = i32
+        lib.ifgf_debug_corrupt_cousin.argtypes = [vp, i32]
+        lib.ifgf_debug_corrupt_cousin.restype = ctypes.c_int
         lib.ifgf_debug_fail_allocation.argtypes = [i64]
         lib.ifgf_debug_fail_allocation.restype = None
         lib.ifgf_debug_drop_cone.argtypes = [vp, i32, i64]
@@ -177,6 +182,11 @@ def release_cached_memory() -> None:
     lib.ifgf_release_cached_memory.argtypes = []
     lib.ifgf_release_cached_memory.restype = ctypes.c_int
     _check(lib.ifgf_release_cached_memory())
+
+
+def checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build (IFGF_CHECKS=1 at load)."""
+    return bool(load().ifgf_checked_build())
 
 
 def debug_fail_allocation(n: int) -> None:
@@ -383,6 +393,11 @@ class Plan:
         n = int(src.shape[0]) if nrhs is None else int(nrhs)
         _check(self._lib.ifgf_permute(self._h, _ptr(src), n, _ptr(dst), 1 if to_sorted else 0, _stream(stream)))
         return dst
+
+    def debug_corrupt_cousin(self, level: int) -> None:
+        """Checked builds only: one cousin entry of `level` becomes a box index past the level's
+        boxes (ifgf_debug_corrupt_cousin), for the next apply's checks to report."""
+        _check(self._lib.ifgf_debug_corrupt_cousin(self._h, int(level)))
 
     def debug_drop_cone(self, level: int, cone: int) -> None:
         """Fault injection for tests: every lookup of relevant cone `cone` of `level` misses from now

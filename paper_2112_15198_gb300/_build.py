@@ -17,7 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, f"libifgf_{platform.machine()}.so")
-SOURCES = ["util.cu", "plan.cu", "apply.cu", "api.cu", "noalloc.cu", "batch.cu", "shard.cu"]
+# the same sources with every bounds check compiled in (-DIFGF_CHECKS)
+CHECKS_LIB = os.path.join(BUILD, f"libifgf_checks_{platform.machine()}.so")
+SOURCES = ["util.cu", "plan.cu", "apply.cu", "api.cu", "noalloc.cu", "batch.cu", "shard.cu", "prop_tc.cu"]
 # throughput probes for the roofline denominators (a library of their own)
 PEAKS_LIB = os.path.join(BUILD, f"libifgf_peaks_{platform.machine()}.so")
 PEAKS_SOURCES = ["peaks.cu"]
@@ -37,17 +39,21 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Build the libraries if a source is newer than them; return the IFGF library's path."""
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    """Build the libraries if a source is newer than them; return the IFGF library's path (the
+    checked variant, compiled with -DIFGF_CHECKS, when checks is true)."""
     os.makedirs(BUILD, exist_ok=True)
-    if not force and all(os.path.exists(f) and os.path.getmtime(f) >= _deps_mtime() for f in (LIB, PEAKS_LIB)):
-        return LIB
+    lib_path = CHECKS_LIB if checks else LIB
+    if not force and all(os.path.exists(f) and os.path.getmtime(f) >= _deps_mtime() for f in (lib_path, PEAKS_LIB)):
+        return lib_path
     nvcc = _nvcc()
-    objs = []
+    tag = "_checks" if checks else ""
+    extra = ["-DIFGF_CHECKS"] if checks else []
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + f"_{platform.machine()}.o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        t = tag if src in SOURCES else ""
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + f"{t}_{platform.machine()}.o")
+        cmd = [nvcc, *ARCH, *FLAGS, *(extra if src in SOURCES else []), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,16 +65,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + len(PEAKS_SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES + PEAKS_SOURCES))
-    for lib, lo in ((LIB, objs[:len(SOURCES)]), (PEAKS_LIB, objs[len(SOURCES):])):
+    for lib, lo in ((lib_path, objs[:len(SOURCES)]), (PEAKS_LIB, objs[len(SOURCES):])):
         tmp = lib + f".tmp{os.getpid()}"
         r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *lo], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, lib)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
     import sys
 
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checks="--checks" in sys.argv))

@@ -227,6 +227,8 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
             if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
                 fail(IFGF_ERR_INVALID_ARG, "points must be device memory");
         }
+        p->d_status = dalloc<int>(*p, 1);
+        IFGF_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
         {
             TimedScope ts_(TK_PLAN, p->stream);
             build_plan(*p, points, opt, levels);
@@ -268,8 +270,6 @@ ifgf_status ifgf_plan_create(const double* points, int64_t N, double kappa, cons
         p->arena = dalloc<char>(*p, (size_t)p->arena_cones * p->rhs_block * p->cstride * csz);
         p->a_s = dalloc<char>(*p, (size_t)N * p->max_nrhs * csz);
         p->I_s = dalloc<char>(*p, (size_t)N * p->max_nrhs * csz);
-        p->d_status = dalloc<int>(*p, 1);
-        IFGF_CUDA(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->stream));
         IFGF_CUDA(cudaStreamSynchronize(p->stream));
     });
     if (st != IFGF_OK) {
@@ -571,6 +571,34 @@ const char* ifgf_last_error(void) { return t_last_error.c_str(); }
 int64_t ifgf_launch_count(void) { return g_launches.load(); }
 
 void ifgf_debug_fail_allocation(int64_t n) { g_fail_alloc_in.store(n > 0 ? n : 0); }
+
+int32_t ifgf_checked_build(void) { return kChecks ? 1 : 0; }
+
+ifgf_status ifgf_debug_corrupt_cousin(ifgf_plan plan, int32_t level) {
+    if (!kChecks) {
+        set_last_error("corrupting a list is allowed in checked builds only");
+        return IFGF_ERR_UNSUPPORTED;
+    }
+    if (!plan || level < 3 || level > plan->D) {
+        set_last_error("NULL plan or level outside [3, D]");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    Plan& p = *plan;
+    return guard([&] {
+        IFGF_CUDA(cudaSetDevice(p.device));
+        IFGF_CUDA(cudaDeviceSynchronize());
+        Level& L = p.L[level];
+        std::vector<int32_t> cnt((size_t)L.n);
+        IFGF_CUDA(cudaMemcpy(cnt.data(), L.ncs, sizeof(int32_t) * L.n, cudaMemcpyDeviceToHost));
+        for (int32_t b = 0; b < L.n; ++b)
+            if (cnt[b] > 0) {
+                const int32_t bad = L.n + 7;  // a box index past the level's boxes
+                IFGF_CUDA(cudaMemcpy(L.cs + (int64_t)b * kMaxCous, &bad, sizeof(int32_t), cudaMemcpyHostToDevice));
+                return;
+            }
+        fail(IFGF_ERR_INVALID_ARG, "no box of the level has a cousin");
+    });
+}
 
 ifgf_status ifgf_permute(ifgf_plan plan, const void* in, int32_t nrhs, void* out, int32_t to_sorted, void* stream) {
     if (!plan || !in || !out || in == out || nrhs < 1) {

@@ -537,14 +537,14 @@ k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_
     constexpr int R = kSegLen / 2;  // a thread evaluates half a segment
     __shared__ float2 s_vals[kWarpCones][8][P];
     __shared__ float4 s_cbuf[kWarpCones][kWarpStage * kStage4];
-    __shared__ int s_slot_w[kWarpCones][8][kTabList];  // global slot, -1 missing, -2 - j staged as block j
+    __shared__ int s_slot_w[kWarpCones][8][kSlotCache];  // global slot, -1 missing, -2 - j staged as block j
     __shared__ int s_row_w[kWarpCones][8], s_goff_w[kWarpCones][9], s_koff_w[kWarpCones][9];
     __shared__ int s_dsl_w[kWarpCones][kWarpStage];  // global slot of every staged block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t pc = (int64_t)blockIdx.x * kWarpCones + warp;
     if (pc >= ncp) return;  // the whole warp leaves; nothing below synchronises the block
     float2 (*vals)[P] = s_vals[warp];
-    int (*s_slot)[kTabList] = s_slot_w[warp];
+    int (*s_slot)[kSlotCache] = s_slot_w[warp];
     int* s_row = s_row_w[warp];
     int* s_goff = s_goff_w[warp];
     const int jb = pcone_box[pc];
@@ -583,7 +583,7 @@ k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_
         const int row = s_row[ch];
         const int Kc = s_koff[ch + 1] - s_koff[ch];
         const int a = __ldg(&tab_list[(int64_t)row * kTabList + lane]);
-        if (lane < Kc) {
+        if (lane < Kc && lane < kSlotCache) {
             const int sl = cm.find(k0 + ch, a);
             const int j = s_koff[ch] + lane;
             const bool staged = sl >= 0 && j < kWarpStage;
@@ -617,7 +617,9 @@ k_prop_warp_f32(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_
         const int sg = __ldg(&tab_seg[rowP + (seg - s_goff[ch])]);
         const int j0 = (sg & 0xff) + R * half, len = min(R, ((sg >> 8) & 0xff) - R * half), kl = sg >> 16;
         if (len <= 0) continue;
-        const int sv = (unsigned)kl < (unsigned)kTabList ? s_slot[ch][kl] : -1;
+        // the rare list positions past the cache (rows whose nodes spread over many child cones)
+        const int sv = kl < kSlotCache ? s_slot[ch][kl]
+                                       : cm.find(k0 + ch, __ldg(&tab_list[(int64_t)s_row[ch] * kTabList + kl]));
         float ts[R], tt[R], tp[R];
         float2 ratio[R], F[R];
 #pragma unroll
@@ -784,6 +786,7 @@ __global__ void __launch_bounds__(kThreads, NR == 1 ? 5 : 4) k_interp_f32(int64_
     const int nc = ncs[A];
     for (int t = 0; t < nc; ++t) {
         const int B = cs[(int64_t)A * kMaxCous + t];
+        if (!in_bounds(B, cm.nbox, status)) continue;
         const int4 kb = kd[B];
         const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
@@ -842,6 +845,7 @@ __global__ void k_interp_f64(int64_t N, int sh, const int32_t* __restrict__ pbox
     double2 acc = make_double2(0., 0.);
     for (int t = 0; t < ncs[A]; ++t) {
         const int B = cs[(int64_t)A * kMaxCous + t];
+        if (!in_bounds(B, cm.nbox, status)) continue;
         const int4 kb = kd[B];
         const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
@@ -1750,7 +1754,7 @@ void launch_interp_f32(Plan& p, int d, int nrhs, float2* Is, cudaStream_t s, Con
 // Interpolation to every target of level d from the level's coefficients.
 template <int PS, int PT, int PP>
 void launch_interp_f32(Plan& p, int d, int nrhs, float2* Is, cudaStream_t s) {
-    launch_interp_f32<PS, PT, PP>(p, d, nrhs, Is, s, p.L[d].cmap(), (const float2*)level_coef(p, d, nrhs), 0, p.N);
+    launch_interp_f32<PS, PT, PP>(p, d, nrhs, Is, s, p.L[d].cmap(p.d_status), (const float2*)level_coef(p, d, nrhs), 0, p.N);
 }
 
 // Levels D..3 of the many-density path: interpolation to the targets of level d (Algorithm 8),
@@ -1774,18 +1778,22 @@ void sweep_levels_mma(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mas
         const float2* cc = (const float2*)level_coef(p, d, nrhs);
         float2* cp = (float2*)level_coef(p, d - 1, nrhs);
         const int64_t cone = (int64_t)nrhs * p.cstride;
-        if (Lp.nc > 0 && Lp.n_gam > 0) {
+        if (Lp.nc > 0 && Lp.n_gam > 0 && nrhs > 8) {
+            // node-table levels, more than 8 densities: tcgen05 products with TMEM accumulators
+            TimedScope ts_(TK_PROP, s);
+            for_each_slice(p, d, [&](int64_t lo, int64_t n) { launch_prop_tc_tab(p, d, nrhs, lo, n, cc, cp + lo * cone, s); });
+        } else if (Lp.nc > 0 && Lp.n_gam > 0) {
             TimedScope ts_(TK_PROP, s);
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
                 IFGF_LAUNCH(k_prop_mma_tab<NT>, dim3((unsigned)n, rb), 16 * NT, 0, s, n, Lp.cone_box + lo,
-                            Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, L.cmap(), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list,
+                            Lp.cone_gidx + lo, Lp.k, Lp.cstart, L.k, L.cmap(p.d_status), Lp.tab_t, Lp.tab_r, Lp.tab_k, Lp.tab_list,
                             Lp.tab_perm, Lp.tab_seg, Lp.tab_run, cc, cp + lo * cone, p.Wf, p.cstride, nrhs, p.d_status);
             });
         } else if (Lp.nc > 0) {
             TimedScope ts_(TK_PROP_GEN, s);
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
                 IFGF_LAUNCH((k_prop_mma<PS, PT, PP, NT>), dim3((unsigned)n, rb), 32 * ((P + kChunk - 1) / kChunk), 0, s,
-                            n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(), L.g, cc,
+                            n, Lp.cone_box + lo, Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(p.d_status), L.g, cc,
                             cp + lo * cone, sh, ku, p.Wf, p.cstride, nrhs, p.d_status);
             });
         }
@@ -1896,7 +1904,7 @@ void sweep_levels_f32(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mas
         const int64_t cone = (int64_t)nrhs * p.cstride;
         if (Lp.nc > 0)
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
-                launch_prop_f32<PS, PT, PP>(p, d, nrhs, lo, n, L.cmap(), cc, cp + lo * cone, s);
+                launch_prop_f32<PS, PT, PP>(p, d, nrhs, lo, n, L.cmap(p.d_status), cc, cp + lo * cone, s);
             });
     }
 }
@@ -1934,7 +1942,7 @@ void sweep_levels_f64(Plan& p, int nrhs, double2* Is, cudaStream_t s, int64_t ma
         if ((mask >> d) & 1) {
             TimedScope ts_(TK_INTERP, s);
             IFGF_LAUNCH((k_interp_f64<PS, PT, PP>), gN, kThreads, 0, s, N, sh, L.pbox, LD.pbox, LD.k, L.k, L.ncs, L.cs,
-                        p.off, p.Xs, L.cmap(), L.g, (const double2*)level_coef(p, d, nrhs), p.kappa, p.a[0], p.a[1],
+                        p.off, p.Xs, L.cmap(p.d_status), L.g, (const double2*)level_coef(p, d, nrhs), p.kappa, p.a[0], p.a[1],
                         p.a[2], Hd, Is, p.cstride, nrhs, p.d_status);
         }
         if (d == 3) break;
@@ -1946,7 +1954,7 @@ void sweep_levels_f64(Plan& p, int nrhs, double2* Is, cudaStream_t s, int64_t ma
             const int64_t cone = (int64_t)nrhs * p.cstride;
             for_each_slice(p, d, [&](int64_t lo, int64_t n) {
                 IFGF_LAUNCH((k_prop_f64<PS, PT, PP>), dim3((unsigned)n, nrhs), BT, 0, s, Lp.cone_box + lo,
-                            Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(), L.g, cc, cp + lo * cone, sh,
+                            Lp.cone_gam + lo, Lp.k, Lp.cstart, Lp.g, L.k, L.cmap(p.d_status), L.g, cc, cp + lo * cone, sh,
                             p.kappa, p.a[0], p.a[1], p.a[2], Hd, p.Wd, p.cstride, nrhs, p.d_status);
             });
         }

@@ -59,6 +59,22 @@ struct LevelGrid {
     const double* pnode64;     // [np*Pp] phi of nodes
 };
 
+// ---- bounds checks (builds with -DIFGF_CHECKS) ------------------------------------------
+// In a checked build the cone lookups test the box and the cone they return, the kernels test
+// the list and table indices they derive before using them, and the plan's index lists are
+// validated once they are built; a failed test records IFGF_ERR_INTERNAL in the plan's status
+// word and the access is skipped.  Other builds compile the tests away.
+#ifdef IFGF_CHECKS
+constexpr bool kChecks = true;
+#else
+constexpr bool kChecks = false;
+#endif
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t n, int* st) {
+    if (!kChecks || (i >= 0 && i < n)) return true;
+    if (st) atomicCAS(st, 0, (int)IFGF_ERR_INTERNAL);
+    return false;
+}
+
 // Cone lookup (box, gamma) -> index of the relevant cone, or -1. Dense levels keep the table
 // slot[box * C + gamma] (one load); levels whose table would be too large keep only the
 // cone list, sorted by (box, gamma), with the first cone of every box (binary search).
@@ -75,11 +91,22 @@ struct ConeMap {
     // A rank of a distributed apply holds some of the level's cones: g2l maps a cone's index in the
     // level's list to its block in the rank's buffer, -1 when the rank does not hold it.
     const int32_t* g2l = nullptr;
+    int32_t nbox = 0;      // boxes of the level (checked builds)
+    int64_t nc = 0;        // relevant cones of the level (checked builds)
+    int* status = nullptr; // status word for failed checks
     __device__ __forceinline__ int find(int box, int gamma) const {
         const int s = find_global(box, gamma);
         return (g2l && s >= 0) ? __ldg(&g2l[s]) : s;
     }
     __device__ __forceinline__ int find_global(int box, int gamma) const {
+        if (!in_bounds(box, nbox, status) || !in_bounds(gamma, C, status)) return -1;
+        if constexpr (kChecks) {
+            const int s = find_unchecked(box, gamma);
+            return in_bounds(s + 1, nc + 1, status) ? s : -1;
+        }
+        return find_unchecked(box, gamma);
+    }
+    __device__ __forceinline__ int find_unchecked(int box, int gamma) const {
         if (slot) return __ldg(&slot[(int64_t)box * C + gamma]);
         int lo, end;
         if (rows) {
@@ -117,7 +144,9 @@ struct Level {
     int32_t* slot = nullptr;       // [n*C] cone index or -1 (dense levels; nullptr when sparse)
     int32_t* bcs = nullptr;        // [n+1] first cone of every box (sparse levels)
     int32_t* rows = nullptr;       // [n * ns * nt + 1] row starts of the cone list (sparse levels)
-    ConeMap cmap() const { return ConeMap{slot, g.C, bcs, cone_gam, rows, g.ns * g.nt, g.np}; }
+    ConeMap cmap(int* st = nullptr) const {
+        return ConeMap{slot, g.C, bcs, cone_gam, rows, g.ns * g.nt, g.np, nullptr, n, nc, st};
+    }
     int32_t* cone_box = nullptr;   // [nc]
     int32_t* cone_gam = nullptr;   // [nc]
     float* phtab = nullptr;        // [28] (kappa H_d sqrt(m)) mod 2 pi, m = |k_A - k_B|^2
@@ -150,7 +179,8 @@ struct Level {
     // Propagation into this level (as the parent level): cone boundaries of its slices.
     std::vector<int64_t> pslice;
 };
-constexpr int kTabList = 32;
+constexpr int kTabList = 80;   // distinct child cones a row may list: at most one per node (75)
+constexpr int kSlotCache = 32; // child-cone slots a warp of the node-table propagation keeps in shared memory
 constexpr int kSegLen = 8;  // nodes of one child cone evaluated by one thread
 constexpr int kChunkBoxes = 8;  // cones (of one gamma, different boxes) per chunk
 
@@ -302,6 +332,10 @@ void shard_interp(Plan& p, int d, int nrhs, float2* Is, const ConeMap& cm, const
                   cudaStream_t s);
 void shard_prop(Plan& p, int d, int nrhs, int64_t lo, int64_t hi, const ConeMap& cm, const float2* cc, float2* cp,
                 cudaStream_t s);
+// Propagation of the parent cones [lo, lo + n) of level d-1 (node tables) for nrhs densities on
+// the tcgen05 tensor cores (prop_tc.cu); child coefficients cc, parent cone lo written at cp.
+void launch_prop_tc_tab(const Plan& p, int d, int nrhs, int64_t lo, int64_t n, const float2* cc, float2* cp,
+                        cudaStream_t s);
 // Caller order <-> sorted order of [nrhs][N] complex vectors of the plan's precision.
 void permute_points(Plan& p, const void* in, int nrhs, void* out, bool to_sorted, cudaStream_t s);
 void apply_plan(Plan& p, const void* dens, int nrhs, void* out, cudaStream_t s, bool near, int64_t mask);

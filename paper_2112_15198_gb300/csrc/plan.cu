@@ -371,7 +371,7 @@ __global__ void k_node_tables(int64_t total, const int32_t* __restrict__ gam_lis
 
 // Distinct child cones of each table row (gamma, octant): the list, and each node's position in
 // it (replacing the cone index in tab_t.w).  Rows are built from the 75-node classification, so
-// K <= 75; the build rejects K > kTabList (the plan then computes that level's geometry).
+// K <= 75 <= kTabList; a row past kTabList would make the build drop the level's tables.
 __global__ void k_node_lists(int P, float4* __restrict__ tab_t, float2* __restrict__ tab_r,
                              int32_t* __restrict__ tab_k, int32_t* __restrict__ tab_list,
                              int16_t* __restrict__ tab_perm, int32_t* __restrict__ tab_nseg,
@@ -836,7 +836,17 @@ void build_node_tables(Plan& p, int dp) {
     const int32_t n_gam = read_one(p, pos + (C - 1)) + read_one(p, flags + (C - 1));
     const int64_t entries = (int64_t)n_gam * 8 * p.P;
     const double sharing = (double)Lp.nc / std::max(1, n_gam);
-    if (sharing >= 4.0 && entries * 30 <= ((int64_t)1 << 30)) {
+    // bytes: 30 per entry (coordinates, ratio, node, segment), lists and runs per row
+    const int64_t bytes = entries * 30 + (int64_t)n_gam * 8 * (2 * kTabList + 3) * 4;
+    // Tables of up to 1 GiB pay off from a sharing of 4; a level whose cone indices are each shared
+    // by hundreds of cones may take up to 8 GiB (and at most 5% of the free device memory).
+    int64_t cap = (int64_t)1 << 30;
+    if (sharing >= 256.0) {
+        size_t free_b = 0, total_b = 0;
+        IFGF_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        cap = std::max(cap, std::min((int64_t)8 << 30, (int64_t)((free_b + pool_cached_bytes(p.device)) / 20)));
+    }
+    if (sharing >= 4.0 && bytes <= cap) {
         Lp.n_gam = n_gam;
         Lp.gam_list = dalloc<int32_t>(p, n_gam);
         Lp.cone_gidx = dalloc<int32_t>(p, Lp.nc);
@@ -875,6 +885,100 @@ void build_node_tables(Plan& p, int dp) {
     }
     dfree_ptr(p, flags);
     dfree_ptr(p, pos);
+}
+
+// ---- validation of the plan's index lists (checked builds) -----------------------------
+// Every index array must address its target array: values in [lo, hi), non-decreasing where they
+// are offsets, and count-aware for the padded neighbour, cousin and table lists.
+__global__ void k_chk_range(const int32_t* __restrict__ a, int64_t n, int64_t lo, int64_t hi, int monotone,
+                            int* __restrict__ st) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    in_bounds((int64_t)a[i] - lo, hi - lo, st);
+    if (monotone && i > 0 && a[i] < a[i - 1]) atomicCAS(st, 0, (int)IFGF_ERR_INTERNAL);
+}
+__global__ void k_chk_range16(const int16_t* __restrict__ a, int64_t n, int hi, int* __restrict__ st) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) in_bounds(a[i], hi, st);
+}
+__global__ void k_chk_lists(const int32_t* __restrict__ cnt, const int32_t* __restrict__ list, int64_t n, int stride,
+                            int maxcnt, int64_t hi, int* __restrict__ st) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int c = cnt[b];
+    if (!in_bounds(c, maxcnt + 1, st)) return;
+    for (int t = 0; t < c; ++t) in_bounds(list[b * stride + t], hi, st);
+}
+// child box k of parent j: k_child - 2 k_parent in {0, 1}^3 (the octant used by the node tables)
+__global__ void k_chk_octants(const int4* __restrict__ kd, const int32_t* __restrict__ parent, int n,
+                              const int4* __restrict__ kp, int np, int* __restrict__ st) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const int j = parent[b];
+    if (!in_bounds(j, np, st)) return;
+    const int ox = kd[b].x - 2 * kp[j].x, oy = kd[b].y - 2 * kp[j].y, oz = kd[b].z - 2 * kp[j].z;
+    in_bounds(ox | oy | oz, 2, st);
+}
+// segments of the node tables: first entry + length within the row, list position within its list
+__global__ void k_chk_segments(const int32_t* __restrict__ nseg, const int32_t* __restrict__ seg,
+                               const int32_t* __restrict__ tab_k, int64_t rows, int P, int* __restrict__ st) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int ns = nseg[r];
+    if (!in_bounds(ns, P + 1, st)) return;
+    for (int t = 0; t < ns; ++t) {
+        const int sg = seg[r * P + t];
+        const int j0 = sg & 0xff, len = (sg >> 8) & 0xff, kl = sg >> 16;
+        in_bounds(j0 + len - 1, P, st);
+        in_bounds(kl, min(tab_k[r], kTabList), st);
+    }
+}
+
+void validate_plan(Plan& p) {
+    cudaStream_t s = p.stream;
+    int* st = p.d_status;
+    const int64_t N = p.N;
+    auto range = [&](const int32_t* a, int64_t n, int64_t lo, int64_t hi, bool mono) {
+        if (a && n > 0) IFGF_LAUNCH(k_chk_range, grid_for(n, kThreads), kThreads, 0, s, a, n, lo, hi, mono ? 1 : 0, st);
+    };
+    range(p.perm, N, 0, N, false);
+    for (int d = 1; d <= p.D; ++d) {
+        Level& L = p.L[d];
+        range(L.start, (int64_t)L.n + 1, 0, N + 1, true);
+        range(L.pbox, N, 0, L.n, true);
+        if (d > 1) {
+            range(L.parent, L.n, 0, p.L[d - 1].n, true);
+            IFGF_LAUNCH(k_chk_octants, grid_for(L.n, kThreads), kThreads, 0, s, L.k, L.parent, L.n, p.L[d - 1].k,
+                        p.L[d - 1].n, st);
+        }
+        if (d < p.D) range(L.cstart, (int64_t)L.n + 1, 0, (int64_t)p.L[d + 1].n + 1, true);
+        if (L.nnb) IFGF_LAUNCH(k_chk_lists, grid_for(L.n, kThreads), kThreads, 0, s, L.nnb, L.nb, L.n, kMaxNbr, kMaxNbr, L.n, st);
+        if (L.ncs) IFGF_LAUNCH(k_chk_lists, grid_for(L.n, kThreads), kThreads, 0, s, L.ncs, L.cs, L.n, kMaxCous, kMaxCous, L.n, st);
+        if (d < 3) continue;
+        range(L.cone_box, L.nc, 0, L.n, true);
+        range(L.cone_gam, L.nc, 0, L.g.C, false);
+        range(L.slot, L.slot ? (int64_t)L.n * L.g.C : 0, -1, L.nc, false);
+        range(L.bcs, L.bcs ? (int64_t)L.n + 1 : 0, 0, L.nc + 1, true);
+        range(L.rows, L.rows ? (int64_t)L.n * L.g.ns * L.g.nt + 1 : 0, 0, L.nc + 1, true);
+        range(L.gorder, L.gorder ? L.nc : 0, 0, L.nc, false);
+        range(L.gchunk, L.gchunk ? L.n_gchunk + 1 : 0, 0, L.nc + 1, true);
+        if (L.n_gam > 0 && d < p.D) {
+            const int64_t rows = (int64_t)L.n_gam * 8;
+            range(L.cone_gidx, L.nc, 0, L.n_gam, false);
+            range(L.gam_list, L.n_gam, 0, L.g.C, true);
+            range(L.tab_k, rows, 0, kTabList + 1, false);
+            range(L.tab_nseg, rows, 0, p.P + 1, false);
+            IFGF_LAUNCH(k_chk_lists, grid_for(rows, kThreads), kThreads, 0, s, L.tab_k, L.tab_list, rows, kTabList,
+                        kTabList, p.L[d + 1].g.C, st);
+            IFGF_LAUNCH(k_chk_segments, grid_for(rows, kThreads), kThreads, 0, s, L.tab_nseg, L.tab_seg, L.tab_k, rows,
+                        p.P, st);
+            IFGF_LAUNCH(k_chk_range16, grid_for(rows * p.P, kThreads), kThreads, 0, s, L.tab_perm, rows * p.P, p.P, st);
+        }
+    }
+    int h = 0;
+    IFGF_CUDA(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IFGF_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) fail(IFGF_ERR_INTERNAL, "plan validation found an index outside its array");
 }
 
 void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
@@ -1097,6 +1201,7 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
             if (L.n_gam == 0) build_gamma_chunks(p, d);
         }
     }
+    if constexpr (kChecks) validate_plan(p);
 }
 
 namespace {

@@ -88,6 +88,7 @@ __global__ void k_look_interp(int64_t p0, int64_t p1, int D, int d, const int32_
     const int sh = D - d;
     for (int t = 0; t < ncs[A]; ++t) {
         const int B = cs[(int64_t)A * kMaxCous + t];
+        if (!in_bounds(B, cm.nbox, status)) continue;
         const int4 kb = kd[B];
         const float vx = __fadd_rn((float)((2 * kl.x + 1) - ((2 * kb.x + 1) << sh)), o.x);
         const float vy = __fadd_rn((float)((2 * kl.y + 1) - ((2 * kb.y + 1) << sh)), o.y);
@@ -269,13 +270,13 @@ ifgf_status ifgf_shard_create(ifgf_plan plan, int32_t nranks, int32_t rank, int3
             IFGF_CUDA(cudaMemsetAsync(fp, 0, nf, s));
             if (sh->p1 > sh->p0)
                 IFGF_LAUNCH(k_look_interp, grid_for(sh->p1 - sh->p0, kT), kT, 0, s, sh->p0, sh->p1, D, d, Lv.pbox, LD.pbox,
-                            LD.k, Lv.k, Lv.ncs, Lv.cs, p.off, Lv.g, Lv.cmap(), fi, p.d_status);
+                            LD.k, Lv.k, Lv.ncs, Lv.cs, p.off, Lv.g, Lv.cmap(p.d_status), fi, p.d_status);
             if (d > 3) {
                 Level& Lp = p.L[d - 1];
                 const int64_t lo = sh->L[d - 1].c0, hi = sh->L[d - 1].c1;
                 if (hi > lo)
                     IFGF_LAUNCH(k_look_prop, grid_for((hi - lo) * p.P, kT), kT, 0, s, lo, hi, p.Ps, p.Pt, p.Pp, D, d,
-                                Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, Lv.k, Lp.g, Lv.g, Lv.cmap(), fp, p.d_status);
+                                Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, Lv.k, Lp.g, Lv.g, Lv.cmap(p.d_status), fp, p.d_status);
             }
             L.looked = to_host(fi, Lv.nc, s);
             const auto lp = to_host(fp, Lv.nc, s);
@@ -423,7 +424,7 @@ ifgf_status ifgf_shard_level(ifgf_shard sh, int32_t level, int32_t nrhs, void* o
         IFGF_CUDA(cudaSetDevice(p.device));
         cudaStream_t s = (cudaStream_t)stream;
         const auto& L = sh->L[level];
-        ConeMap cm = p.L[level].cmap();
+        ConeMap cm = p.L[level].cmap(p.d_status);
         cm.g2l = L.g2l;
         shard_interp(p, level, nrhs, (float2*)out_sorted, cm, L.coef, sh->p0, sh->p1, s);
         if (level > 3) {

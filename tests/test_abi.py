@@ -157,3 +157,20 @@ def test_batch_rejects_a_repeated_plan(lib):
     assert lib.ifgf_batch_create(plans, 3, ctypes.byref(h)) == 1
     assert b"repeats" in lib.ifgf_last_error()
     assert lib.ifgf_batch_create(plans, 0, ctypes.byref(h)) == 1
+
+
+def test_checked_build_exports_the_same_entry_points():
+    """The bounds-checked variant (-DIFGF_CHECKS) builds for sm_103a, exports every declared function
+    and says it is checked; host-side validation behaves as in the ordinary build."""
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2112_15198_gb300 import _build
+
+    chk = ctypes.CDLL(_build.build(checks=True))
+    for name in _declared_functions():
+        assert hasattr(chk, name), name
+    chk.ifgf_checked_build.restype = ctypes.c_int32
+    assert chk.ifgf_checked_build() == 1
+    h = ctypes.c_void_p()
+    chk.ifgf_plan_create.restype = ctypes.c_int
+    assert chk.ifgf_plan_create(None, 10, ctypes.c_double(1.0), None, 0, None, None, ctypes.byref(h)) == 1
