@@ -235,6 +235,27 @@ enum {
 };
 ifgf_status ifgf_plan_query(ifgf_plan plan, int32_t what, int32_t level, int64_t* host_buf, int64_t* inout_count);
 
+typedef enum { IFGF_KNOB_PROP_MANY = 0, IFGF_KNOB_PROP_FEW = 1, IFGF_KNOB_RHS_BLOCK = 2 } ifgf_knob;
+/*
+ * Kernel choices ("knobs") of a plan's mixed-precision apply.  Every choice computes the same
+ * values of Algorithm 7; they differ in speed and in the rounding order of the FP32 sums.  A
+ * value of -1 restores the built-in choice.
+ *   IFGF_KNOB_PROP_MANY, per level d (the propagation from level d into level d-1, 4 <= d <= D),
+ *     in effect where level d-1 has node tables and nrhs >= 4: 0 warp-level mma.sync tiles
+ *     (built-in), 1 tcgen05 products with TMEM accumulators; both 3xTF32.
+ *   IFGF_KNOB_PROP_FEW, per level d, in effect where level d-1 has node tables and nrhs < 4:
+ *     0 the node-table warp kernel (built-in), 1 the per-cone kernel that computes the geometry.
+ *   IFGF_KNOB_RHS_BLOCK, plan-wide (level ignored), nrhs >= 4: densities per block of the
+ *     many-density kernels, 8, 16 or 32 (built-in, -1: the smallest of them >= nrhs, else 32).
+ * ifgf_plan_get_knob returns the choice in effect for a level knob (-1 where level d-1 has no
+ * node tables, so that the knob has no effect) and the value set for IFGF_KNOB_RHS_BLOCK.
+ * Host only, no synchronisation; the next apply uses the new choice.
+ * Errors: IFGF_ERR_INVALID_ARG (NULL plan or value pointer, unknown knob, level or value out of
+ * range).
+ */
+ifgf_status ifgf_plan_set_knob(ifgf_plan plan, int32_t knob, int32_t level, int32_t value);
+ifgf_status ifgf_plan_get_knob(ifgf_plan plan, int32_t knob, int32_t level, int32_t* value);
+
 /*
  * Distribution over several GPUs (Sec. 3.2), one rank per GPU.
  *

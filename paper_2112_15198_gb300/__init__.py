@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["IFGFError", "Plan", "Batch", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q",
+__all__ = ["IFGFError", "Plan", "Batch", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q", "KNOB",
            "debug_fail_allocation", "Shard", "SQ", "partition_boxes", "partition_cones",
            "PREC_FP64", "PREC_MIXED"]
 
@@ -32,6 +32,12 @@ class Q:
     NBR_COUNT, NBR_LIST, COUS_COUNT, COUS_LIST = 5, 6, 7, 8
     CONE_BOX, CONE_GAMMA, GRID, INFO, WORK, STATUS, CHILD_START, BOX_COORDS = 9, 10, 11, 12, 13, 14, 15, 16
     TABLES = 17
+
+
+class KNOB:
+    """Kernel choices of ifgf_plan_set_knob."""
+
+    PROP_MANY, PROP_FEW, RHS_BLOCK = 0, 1, 2
 
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "INTERNAL", 6: "UNSUPPORTED"}
@@ -138,6 +144,10 @@ def load(build: bool = True):
         lib.ifgf_shard_level.restype = ctypes.c_int
         lib.ifgf_shard_destroy.argtypes = [vp]
         lib.ifgf_shard_destroy.restype = ctypes.c_int
+        lib.ifgf_plan_set_knob.argtypes = [vp, i32, i32, i32]
+        lib.ifgf_plan_set_knob.restype = ctypes.c_int
+        lib.ifgf_plan_get_knob.argtypes = [vp, i32, i32, ctypes.POINTER(i32)]
+        lib.ifgf_plan_get_knob.restype = ctypes.c_int
         lib.ifgf_permute.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.ifgf_permute.restype = ctypes.c_int
         lib.ifgf_timing_enable.argtypes = [i32]
@@ -398,6 +408,17 @@ class Plan:
         """Checked builds only: one cousin entry of `level` becomes a box index past the level's
         boxes (ifgf_debug_corrupt_cousin), for the next apply's checks to report."""
         _check(self._lib.ifgf_debug_corrupt_cousin(self._h, int(level)))
+
+    def set_knob(self, knob: int, level: int, value: int) -> None:
+        """Kernel choice of the apply (ifgf_plan_set_knob): KNOB.PROP_MANY / KNOB.PROP_FEW per level
+        d of the propagation from d into d-1, KNOB.RHS_BLOCK plan-wide; -1 restores the built-in."""
+        _check(self._lib.ifgf_plan_set_knob(self._h, int(knob), int(level), int(value)))
+
+    def get_knob(self, knob: int, level: int = 0) -> int:
+        """The kernel choice in effect (ifgf_plan_get_knob)."""
+        v = ctypes.c_int32(0)
+        _check(self._lib.ifgf_plan_get_knob(self._h, int(knob), int(level), ctypes.byref(v)))
+        return int(v.value)
 
     def debug_drop_cone(self, level: int, cone: int) -> None:
         """Fault injection for tests: every lookup of relevant cone `cone` of `level` misses from now

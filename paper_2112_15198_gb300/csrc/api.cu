@@ -611,6 +611,52 @@ ifgf_status ifgf_permute(ifgf_plan plan, const void* in, int32_t nrhs, void* out
     });
 }
 
+ifgf_status ifgf_plan_set_knob(ifgf_plan plan, int32_t knob, int32_t level, int32_t value) {
+    if (!plan) {
+        set_last_error("NULL plan");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    Plan& p = *plan;
+    if (knob == IFGF_KNOB_RHS_BLOCK) {
+        if (value != -1 && value != 8 && value != 16 && value != 32) {
+            set_last_error("densities per block must be 8, 16 or 32 (or -1)");
+            return IFGF_ERR_INVALID_ARG;
+        }
+        p.knob_block = value;
+        return IFGF_OK;
+    }
+    if (knob != IFGF_KNOB_PROP_MANY && knob != IFGF_KNOB_PROP_FEW) {
+        set_last_error("unknown knob");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    if (level < 4 || level > p.D || value < -1 || value > 1) {
+        set_last_error("knob level must be in [4, D] and its value in {-1, 0, 1}");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    (knob == IFGF_KNOB_PROP_MANY ? p.L[level].knob_many : p.L[level].knob_few) = (int8_t)value;
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_plan_get_knob(ifgf_plan plan, int32_t knob, int32_t level, int32_t* value) {
+    if (!plan || !value) {
+        set_last_error("NULL plan or value pointer");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    Plan& p = *plan;
+    if (knob == IFGF_KNOB_RHS_BLOCK) {
+        *value = p.knob_block;
+        return IFGF_OK;
+    }
+    if ((knob != IFGF_KNOB_PROP_MANY && knob != IFGF_KNOB_PROP_FEW) || level < 4 || level > p.D) {
+        set_last_error("unknown knob or level out of [4, D]");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    const Level& L = p.L[level];
+    const int v = knob == IFGF_KNOB_PROP_MANY ? L.knob_many : L.knob_few;
+    *value = p.L[level - 1].n_gam > 0 ? (v < 0 ? 0 : v) : -1;
+    return IFGF_OK;
+}
+
 ifgf_status ifgf_debug_drop_cone(ifgf_plan plan, int32_t level, int64_t cone) {
     if (!plan) {
         set_last_error("NULL plan");

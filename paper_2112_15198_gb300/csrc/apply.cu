@@ -1778,8 +1778,8 @@ void sweep_levels_mma(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mas
         const float2* cc = (const float2*)level_coef(p, d, nrhs);
         float2* cp = (float2*)level_coef(p, d - 1, nrhs);
         const int64_t cone = (int64_t)nrhs * p.cstride;
-        if (Lp.nc > 0 && Lp.n_gam > 0 && nrhs > 8) {
-            // node-table levels, more than 8 densities: tcgen05 products with TMEM accumulators
+        if (Lp.nc > 0 && Lp.n_gam > 0 && L.knob_many == 1) {
+            // node-table levels on the fifth-generation tensor cores (tcgen05, TMEM accumulators)
             TimedScope ts_(TK_PROP, s);
             for_each_slice(p, d, [&](int64_t lo, int64_t n) { launch_prop_tc_tab(p, d, nrhs, lo, n, cc, cp + lo * cone, s); });
         } else if (Lp.nc > 0 && Lp.n_gam > 0) {
@@ -1864,7 +1864,7 @@ void launch_prop_f32(Plan& p, int d, int nrhs, int64_t lo, int64_t n, ConeMap cm
     const int sh = p.D - d;
     const float ku = (float)(p.kappa * p.u);
     if (n <= 0) return;
-    if (Lp.n_gam > 0 && PS * PT * PP <= 75) {  // tables are built for (3,5,5) only
+    if (Lp.n_gam > 0 && PS * PT * PP <= 75 && L.knob_few != 1) {  // tables are built for (3,5,5) only
         TimedScope ts_(TK_PROP, s);
         constexpr int TS = PS * PT * PP <= 75 ? PS : 3, TT = PS * PT * PP <= 75 ? PT : 5,
                       TP = PS * PT * PP <= 75 ? PP : 5;
@@ -1914,9 +1914,10 @@ template <int PS, int PT, int PP>
 void sweep_levels_mixed(Plan& p, int nrhs, float2* Is, cudaStream_t s, int64_t mask) {
     if constexpr (PS == 3 && PT == 5 && PP == 5) {
         if (nrhs >= kMmaMinRhs) {
-            if (nrhs <= 8)
+            const int blk = p.knob_block > 0 ? p.knob_block : nrhs <= 8 ? 8 : nrhs <= 16 ? 16 : 32;
+            if (blk == 8)
                 sweep_levels_mma<2, PS, PT, PP>(p, nrhs, Is, s, mask);
-            else if (nrhs <= 16)
+            else if (blk == 16)
                 sweep_levels_mma<4, PS, PT, PP>(p, nrhs, Is, s, mask);
             else
                 sweep_levels_mma<8, PS, PT, PP>(p, nrhs, Is, s, mask);

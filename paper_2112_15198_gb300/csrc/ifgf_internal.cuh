@@ -178,6 +178,12 @@ struct Level {
     int32_t* gchunk = nullptr;     // [n_gchunk+1]
     // Propagation into this level (as the parent level): cone boundaries of its slices.
     std::vector<int64_t> pslice;
+    // Kernel choices of the propagation from this level into level d-1 where level d-1 has node
+    // tables (-1: the built-in choice), set by ifgf_plan_set_knob or the autotuner:
+    //   knob_many (mixed, kMmaMinRhs densities or more): 0 mma.sync tiles, 1 tcgen05 + TMEM;
+    //   knob_few (mixed, fewer densities): 0 the node-table warp kernel, 1 the per-cone kernel.
+    int8_t knob_many = -1;
+    int8_t knob_few = -1;
 };
 constexpr int kTabList = 80;   // distinct child cones a row may list: at most one per node (75)
 constexpr int kSlotCache = 32; // child-cone slots a warp of the node-table propagation keeps in shared memory
@@ -193,6 +199,7 @@ struct Plan {
     int precision = IFGF_PREC_MIXED;
     int max_nrhs = 1;
     int rhs_block = 1;             // densities per level sweep (coefficient buffers hold this many)
+    int knob_block = -1;           // densities per block of the many-density kernels (8, 16, 32; -1 by nrhs)
     double a[3] = {0, 0, 0};
     double H1 = 0, u = 0;
     int device = 0;

@@ -337,6 +337,58 @@ def test_many_densities_tensor_core_path(nrhs, shape):
     assert oracle.rel_l2(got[nrhs - 1], single) < 2e-5
 
 
+@pytest.mark.parametrize("nrhs,block", [(12, -1), (32, -1), (20, 8), (6, 32)])
+def test_tcgen05_products_and_density_blocks(nrhs, block):
+    """The kernel choices of the many-density path: on every level whose parent level has node
+    tables, the propagation as tcgen05 products with TMEM accumulators (knob PROP_MANY = 1) or as
+    mma.sync tiles, with 8, 16 or 32 densities per block; every density matches the CPU IFGF, and
+    the two product kernels agree to FP32 rounding."""
+    n = 9000
+    pts = W.spheroid(n, 0.5, 0.125, seed=33)
+    kappa = 2 * math.pi * 6
+    A = W.densities(n, nrhs, 23)
+    ref = oracle.Plan(pts, kappa).apply(A)
+    gp = _plan(pts, kappa, precision="mixed", max_nrhs=nrhs)
+    gp.set_knob(ifgf.KNOB.RHS_BLOCK, 0, block)
+    tab = [d for d in range(4, gp.D + 1) if gp.get_knob(ifgf.KNOB.PROP_MANY, d) >= 0]
+    assert tab, "no level with node tables"
+    mma = _apply(gp, A, "mixed")
+    for d in tab:
+        gp.set_knob(ifgf.KNOB.PROP_MANY, d, 1)
+        assert gp.get_knob(ifgf.KNOB.PROP_MANY, d) == 1
+    tc = _apply(gp, A, "mixed")
+    assert gp.status() == 0
+    for r in range(nrhs):
+        assert oracle.rel_l2(tc[r], ref[r]) < 3e-5, r
+        assert oracle.rel_l2(mma[r], ref[r]) < 3e-5, r
+        assert oracle.rel_l2(tc[r], mma[r]) < 1e-5, r
+
+
+def test_per_cone_kernel_on_table_levels():
+    """With one density, the per-cone propagation (knob PROP_FEW = 1) on the node-table levels
+    gives the values of the node-table warp kernel up to FP32 rounding, and both match the CPU
+    IFGF."""
+    pts = W.fibonacci_sphere(9000)
+    kappa = 2 * math.pi * 6
+    A = W.densities(9000, 1, 5)
+    ref = oracle.Plan(pts, kappa).apply(A)
+    gp = _plan(pts, kappa, precision="mixed")
+    warp = _apply(gp, A, "mixed")
+    tab = [d for d in range(4, gp.D + 1) if gp.get_knob(ifgf.KNOB.PROP_FEW, d) >= 0]
+    assert tab
+    for d in tab:
+        gp.set_knob(ifgf.KNOB.PROP_FEW, d, 1)
+    cone = _apply(gp, A, "mixed")
+    assert gp.status() == 0
+    assert oracle.rel_l2(warp[0], ref[0]) < 3e-5
+    assert oracle.rel_l2(cone[0], ref[0]) < 3e-5
+    assert oracle.rel_l2(cone[0], warp[0]) < 1e-5
+    with pytest.raises(ifgf.IFGFError):
+        gp.set_knob(ifgf.KNOB.PROP_FEW, 3, 1)
+    with pytest.raises(ifgf.IFGFError):
+        gp.set_knob(ifgf.KNOB.RHS_BLOCK, 0, 12)
+
+
 @pytest.mark.parametrize("stage", ["near", "leaf_level", "top_level"])
 def test_many_densities_stages(stage):
     w = W.make("sphere4")
