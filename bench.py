@@ -173,14 +173,15 @@ def algorithmic_flops(work: dict, ncone: dict, P: int, sets: int, stokes_fields:
     return {"prop": prop["prop"], "prop_gen": prop["prop_gen"], "interp": interp, "leaf": leaf, "near": near}
 
 
-def kernel_source_sha(kernel: str, apply_src: str, header_src: str) -> str:
-    """sha256 prefix of a kernel's definition in apply.cu together with the device helpers of
-    ifgf_internal.cuh (everything after its "Device helpers" banner)."""
+def kernel_source_sha(kernel: str, apply_src: str, header_src: str, bodies_src: str = "") -> str:
+    """sha256 prefix of a kernel's definition in apply.cu together with the device bodies it
+    runs (bodies_f32.cuh) and the device helpers of ifgf_internal.cuh (everything after its
+    "Device helpers" banner)."""
     at = apply_src.index(f"\n{kernel}(")
     start = apply_src.rindex("\n\n", 0, at)
     end = apply_src.index("\n}\n", at) + 3
     dev = header_src[header_src.index("// Device helpers"):]
-    return hashlib.sha256((apply_src[start:end] + dev).encode()).hexdigest()[:16]
+    return hashlib.sha256((apply_src[start:end] + bodies_src + dev).encode()).hexdigest()[:16]
 
 
 def traffic_record(kernel: str):
@@ -192,7 +193,8 @@ def traffic_record(kernel: str):
     csrc = os.path.join(ROOT, "paper_2112_15198_gb300", "csrc")
     try:
         sha = kernel_source_sha(kernel, open(os.path.join(csrc, "apply.cu")).read(),
-                                open(os.path.join(csrc, "ifgf_internal.cuh")).read())
+                                open(os.path.join(csrc, "ifgf_internal.cuh")).read(),
+                                open(os.path.join(csrc, "bodies_f32.cuh")).read())
     except ValueError:
         return None
     for ln in open(path):

@@ -185,26 +185,87 @@ ifgf_status ifgf_apply_elastic_ex(ifgf_plan plan, const void* forces, int32_t nf
  * ifgf_release_cached_memory).  NULL is accepted. */
 ifgf_status ifgf_plan_destroy(ifgf_plan plan);
 
+/* Settings of ifgf_batch_set / ifgf_batch_get (described below). */
+typedef enum {
+    IFGF_BATCH_MODE = 0,
+    IFGF_BATCH_CONES_PER_ITEM = 1,
+    IFGF_BATCH_BLOCKS_PER_SM = 2,
+    IFGF_BATCH_WAIT_LIMIT = 3,
+    IFGF_BATCH_WITHHOLD = 4,
+    IFGF_BATCH_STATUS = 5,
+    IFGF_BATCH_LAST_MODE = 6,
+    IFGF_BATCH_ITEMS = 7
+} ifgf_batch_setting;
 /*
  * Batched evaluation of many independent problems (each its own plan, e.g. bodies of different
- * sizes) as one launch sequence: the operator of Eq. (1) is applied to every plan.  The first
- * ifgf_batch_apply with a given set of buffers captures the applies into a CUDA graph on private
- * streams (plan i on branch i mod 8 of a fork/join, so that independent problems run
- * concurrently; each result is the same as the plan's own apply); later calls with the same
- * buffers replay that graph with one launch on
- * `stream` (other buffers trigger a new capture).  Plans must live on one device, must outlive
- * the batch, and must not be applied elsewhere while the batch runs (they own their scratch).
+ * sizes): the operator of Eq. (1) is applied to every plan, and each result is bit-identical to
+ * the plan's own ifgf_apply.  Two launch sequences are built:
+ *   queue  (plans of mixed precision with orders (3,5,5), one density each) one short sequence
+ *          over work lists that mix all problems, largest first: permutation in, near field,
+ *          LevelDEvaluations (Algorithm 6), one persistent propagation kernel (Algorithm 7) for
+ *          every level of every problem, interpolation (Algorithm 8) and permutation out.  The
+ *          propagation's blocks take runs of parent cones from a queue ordered by the distance of
+ *          the child level from the problem's leaves; a run whose child level is not complete
+ *          waits on the problem's per-level counter (waits bounded by IFGF_BATCH_WAIT_LIMIT
+ *          polls, see ifgf_batch_set).  It keeps the coefficients of every level of every
+ *          problem (device memory owned by the batch, allocated at the first queue apply).
+ *   graph  (any plans) each plan's own apply captured on branch i mod 8 of a fork/join, so that
+ *          independent problems run concurrently.
+ * Either sequence is captured into a CUDA graph by the first ifgf_batch_apply and replayed with
+ * one graph launch on `stream` by later calls (the graph sequence is captured again when the
+ * buffers change; the queue sequence reads the buffer pointers from a table that the call
+ * updates, synchronising `stream` when they changed).  Plans must live on one device, must
+ * outlive the batch, and must not be applied elsewhere while the batch runs (they own their
+ * scratch).  Kernel knobs of the plans are read when the queue is built.
  *
  *   plans  n distinct plan handles (not owned); a handle that appears twice returns
  *          IFGF_ERR_INVALID_ARG, since each plan's buffers can serve one problem at a time.
  *   dens   n device pointers, plan i's densities as in ifgf_apply.
  *   nrhs   n counts, 1 <= nrhs[i] <= that plan's max_nrhs.
  *   outs   n device pointers, plan i's outputs.
+ *
+ * ifgf_batch_set / ifgf_batch_get (host; a change takes effect at the next apply):
+ *   IFGF_BATCH_MODE            -1 queue where the plans allow it, else graph (default); 0 graph;
+ *                              1 queue (ifgf_batch_apply returns IFGF_ERR_UNSUPPORTED when the
+ *                              plans do not allow it).
+ *   IFGF_BATCH_CONES_PER_ITEM  parent cones per propagation queue item, >= 4 (rounded down to a
+ *                              multiple of 4; default 16).
+ *   IFGF_BATCH_BLOCKS_PER_SM   resident blocks per SM of the persistent propagation (0: as many
+ *                              as fit, the default).
+ *   IFGF_BATCH_WAIT_LIMIT      polls of a dependency counter (about 0.3 us each) before the
+ *                              waiting block records IFGF_ERR_TIMEOUT in the batch's status word
+ *                              and skips its item; later waits then give up at once (default 2^24).
+ *   IFGF_BATCH_WITHHOLD        test only: problem * 64 + level d (4 <= d <= D of that problem):
+ *                              the first queue item of the propagation from level d is never
+ *                              counted as complete, so the items of level d-1 wait until their
+ *                              limit; -1 turns it off.
+ *   get only: IFGF_BATCH_STATUS (synchronises the device; the status word of the last queue
+ *   sequence, IFGF_OK or IFGF_ERR_TIMEOUT, reset by every queue apply), IFGF_BATCH_LAST_MODE (the
+ *   sequence the last apply ran: 0 graph, 1 queue, -1 none), IFGF_BATCH_ITEMS (propagation
+ *   queue items of the last queue sequence).
+ * Errors: IFGF_ERR_INVALID_ARG for a NULL handle or pointer, an unknown code or a value out of
+ * range.
  */
 ifgf_status ifgf_batch_create(const ifgf_plan* plans, int32_t n, ifgf_batch* out_batch);
 ifgf_status ifgf_batch_apply(ifgf_batch batch, const void* const* dens, const int32_t* nrhs, void* const* outs,
                              void* stream);
 ifgf_status ifgf_batch_destroy(ifgf_batch batch);
+ifgf_status ifgf_batch_set(ifgf_batch batch, int32_t what, int64_t value);
+ifgf_status ifgf_batch_get(ifgf_batch batch, int32_t what, int64_t* value);
+
+/*
+ * Autotuner of a batch: times ifgf_batch_apply with the given buffers (three replays after a
+ * warm-up) for the graph sequence and, where the plans allow it, the queue sequence with 8, 16,
+ * 32 and 64 parent cones per item and 0 or 2 blocks per SM; sets the fastest (IFGF_BATCH_MODE,
+ * IFGF_BATCH_CONES_PER_ITEM, IFGF_BATCH_BLOCKS_PER_SM).  Choices are cached in cache_path (NULL:
+ * no cache) under a key of the GPU, the number of problems, their total and largest N (floor
+ * log2 each), the densities bucket and whether the queue applies; with a cache hit nothing is
+ * measured.  The outputs hold a valid result of the batch afterwards.  Arguments as
+ * ifgf_batch_apply; from_cache: optional output, 1 if nothing was measured.
+ * Errors: those of ifgf_batch_apply, IFGF_ERR_INVALID_ARG for an unwritable cache.
+ */
+ifgf_status ifgf_batch_autotune(ifgf_batch batch, const void* const* dens, const int32_t* nrhs, void* const* outs,
+                                const char* cache_path, void* stream, int32_t* from_cache);
 
 /*
  * Introspection (synchronous).  Copies the requested array into host_buf as int64 values
@@ -255,6 +316,29 @@ typedef enum { IFGF_KNOB_PROP_MANY = 0, IFGF_KNOB_PROP_FEW = 1, IFGF_KNOB_RHS_BL
  */
 ifgf_status ifgf_plan_set_knob(ifgf_plan plan, int32_t knob, int32_t level, int32_t value);
 ifgf_status ifgf_plan_get_knob(ifgf_plan plan, int32_t knob, int32_t level, int32_t* value);
+
+/*
+ * Autotuner of the knobs above: for an apply with nrhs densities it times, on the plan's own
+ * tree and cones with synthetic densities, each candidate kernel of every level whose parent
+ * level has node tables (per-level propagation times from CUDA events around the launches) and,
+ * from 4 densities on, each density block (8, 16, 32, by the time of the whole apply with the
+ * faster kernel on every level), and sets the fastest.  The choices are stored in the text file
+ * cache_path (created or rewritten whole; NULL: no cache) under keys made of the GPU's name and
+ * SM count, the orders, the densities bucket (1, 2-3, 4-8, 9-16, 17-32, 33+) and the size
+ * bucket (floor log2 of the level's cone counts, of N for the block); when every key is already
+ * there the choices are taken from the file without measuring.  Plans other than mixed
+ * precision with orders (3,5,5) have no choices: the call returns IFGF_OK and changes nothing.
+ *
+ *   nrhs        1 <= nrhs <= the plan's max_nrhs.
+ *   stream      cudaStream_t as void*; the measurement runs on it (about six applies for
+ *               1-3 densities, fourteen from 4 on) and the call returns after it.
+ *   from_cache  optional output: 1 if nothing was measured.
+ * The library's kernel timing (ifgf_timing_enable) is used and its collected totals are
+ * discarded.  Errors: IFGF_ERR_INVALID_ARG (NULL plan, nrhs out of range, unwritable cache),
+ * IFGF_ERR_OOM, IFGF_ERR_CUDA.
+ */
+ifgf_status ifgf_plan_autotune(ifgf_plan plan, int32_t nrhs, const char* cache_path, void* stream,
+                               int32_t* from_cache);
 
 /*
  * Distribution over several GPUs (Sec. 3.2), one rank per GPU.

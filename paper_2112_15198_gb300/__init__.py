@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["IFGFError", "Plan", "Batch", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q", "KNOB",
+__all__ = ["IFGFError", "Plan", "Batch", "load", "library_path", "launch_count", "timing_enable", "timing_collect", "Q", "KNOB", "BATCH",
            "debug_fail_allocation", "Shard", "SQ", "partition_boxes", "partition_cones",
            "PREC_FP64", "PREC_MIXED"]
 
@@ -32,6 +32,12 @@ class Q:
     NBR_COUNT, NBR_LIST, COUS_COUNT, COUS_LIST = 5, 6, 7, 8
     CONE_BOX, CONE_GAMMA, GRID, INFO, WORK, STATUS, CHILD_START, BOX_COORDS = 9, 10, 11, 12, 13, 14, 15, 16
     TABLES = 17
+
+
+class BATCH:
+    """Settings and states of ifgf_batch_set / ifgf_batch_get."""
+
+    MODE, CONES_PER_ITEM, BLOCKS_PER_SM, WAIT_LIMIT, WITHHOLD, STATUS, LAST_MODE, ITEMS = range(8)
 
 
 class KNOB:
@@ -114,6 +120,15 @@ def load(build: bool = True):
         lib.ifgf_batch_create.restype = ctypes.c_int
         lib.ifgf_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp), vp]
         lib.ifgf_batch_apply.restype = ctypes.c_int
+        lib.ifgf_batch_set.argtypes = [vp, i32, i64]
+        lib.ifgf_batch_set.restype = ctypes.c_int
+        lib.ifgf_batch_get.argtypes = [vp, i32, ctypes.POINTER(i64)]
+        lib.ifgf_batch_get.restype = ctypes.c_int
+        lib.ifgf_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp),
+                                            ctypes.c_char_p, vp, ctypes.POINTER(i32)]
+        lib.ifgf_batch_autotune.restype = ctypes.c_int
+        lib.ifgf_plan_autotune.argtypes = [vp, i32, ctypes.c_char_p, vp, ctypes.POINTER(i32)]
+        lib.ifgf_plan_autotune.restype = ctypes.c_int
         lib.ifgf_batch_destroy.argtypes = [vp]
         lib.ifgf_batch_destroy.restype = ctypes.c_int
         lib.ifgf_checked_build.argtypes = []
@@ -414,6 +429,14 @@ class Plan:
         d of the propagation from d into d-1, KNOB.RHS_BLOCK plan-wide; -1 restores the built-in."""
         _check(self._lib.ifgf_plan_set_knob(self._h, int(knob), int(level), int(value)))
 
+    def autotune(self, nrhs: int = 1, cache_path=None, stream=None) -> bool:
+        """Times the kernel choices of an apply with nrhs densities and keeps the fastest
+        (ifgf_plan_autotune); True if they came from the cache file."""
+        hit = ctypes.c_int32(0)
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(self._lib.ifgf_plan_autotune(self._h, int(nrhs), path, _stream(stream), ctypes.byref(hit)))
+        return bool(hit.value)
+
     def get_knob(self, knob: int, level: int = 0) -> int:
         """The kernel choice in effect (ifgf_plan_get_knob)."""
         v = ctypes.c_int32(0)
@@ -463,7 +486,8 @@ class Plan:
 
 
 class Batch:
-    """Many plans applied as one CUDA-graph launch sequence (ifgf_batch_*)."""
+    """Many plans applied as one captured launch sequence (ifgf_batch_*): work queues over all
+    problems where the plans allow it, else each plan's apply on concurrent graph branches."""
 
     def __init__(self, plans):
         lib = load()
@@ -483,6 +507,30 @@ class Batch:
         r = (ctypes.c_int32 * n)(*(int(x) for x in nrhs_list))
         _check(self._lib.ifgf_batch_apply(self._h, d, r, o, _stream(stream)))
         return out_list
+
+    def autotune(self, dens_list, out_list, cache_path=None, nrhs_list=None, stream=None) -> bool:
+        """Times the batch's launch sequences and settings and keeps the fastest
+        (ifgf_batch_autotune); True if the choice came from the cache file."""
+        n = len(self._plans)
+        if nrhs_list is None:
+            nrhs_list = [1 if len(d.shape) == 1 else int(d.shape[0]) for d in dens_list]
+        d = (ctypes.c_void_p * n)(*(_ptr(x) for x in dens_list))
+        o = (ctypes.c_void_p * n)(*(_ptr(x) for x in out_list))
+        r = (ctypes.c_int32 * n)(*(int(x) for x in nrhs_list))
+        hit = ctypes.c_int32(0)
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(self._lib.ifgf_batch_autotune(self._h, d, r, o, path, _stream(stream), ctypes.byref(hit)))
+        return bool(hit.value)
+
+    def set(self, what: int, value: int) -> None:
+        """A setting of the batch (ifgf_batch_set), e.g. BATCH.MODE or BATCH.CONES_PER_ITEM."""
+        _check(self._lib.ifgf_batch_set(self._h, int(what), int(value)))
+
+    def get(self, what: int) -> int:
+        """A setting or state of the batch (ifgf_batch_get); BATCH.STATUS synchronises."""
+        v = ctypes.c_int64(0)
+        _check(self._lib.ifgf_batch_get(self._h, int(what), ctypes.byref(v)))
+        return int(v.value)
 
     def destroy(self):
         h = getattr(self, "_h", None)

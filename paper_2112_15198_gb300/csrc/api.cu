@@ -33,9 +33,10 @@ struct TimingState {
     std::mutex mu;
     bool on = false;
     std::vector<cudaEvent_t> pool;
-    std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>> pending;  // kind, level, start, end
     double ms[TK_COUNT] = {0};
     int64_t launches[TK_COUNT] = {0};
+    double by_level[TK_COUNT][kMaxLevel + 1] = {};
     cudaEvent_t get() {
         if (!pool.empty()) {
             cudaEvent_t e = pool.back();
@@ -51,9 +52,47 @@ TimingState& timing() {
     static TimingState t;
     return t;
 }
+thread_local int g_timing_level = -1;
 }  // namespace
 
-TimedScope::TimedScope(int k, cudaStream_t s) : kind(k), stream(s) {
+TimingLevel::TimingLevel(int d) : prev(g_timing_level) { g_timing_level = d; }
+TimingLevel::~TimingLevel() { g_timing_level = prev; }
+
+bool timing_switch(bool on) {
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> lk(t.mu);
+    const bool was = t.on;
+    t.on = on;
+    return was;
+}
+
+void timing_collect_levels(double* ms, int64_t* launches, double (*by_level)[kMaxLevel + 1]) {
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> lk(t.mu);
+    for (auto& [k, lev, a, b] : t.pending) {
+        float el = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&el, a, b) != cudaSuccess)
+            cuda_check(cudaGetLastError(), "kernel timing");
+        t.ms[k] += el;
+        t.launches[k] += 1;
+        if (lev >= 0 && lev <= kMaxLevel) t.by_level[k][lev] += el;
+        t.pool.push_back(a);
+        t.pool.push_back(b);
+    }
+    t.pending.clear();
+    for (int k = 0; k < TK_COUNT; ++k) {
+        if (ms) ms[k] = t.ms[k];
+        if (launches) launches[k] = t.launches[k];
+        for (int d = 0; d <= kMaxLevel; ++d) {
+            if (by_level) by_level[k][d] = t.by_level[k][d];
+            t.by_level[k][d] = 0;
+        }
+        t.ms[k] = 0;
+        t.launches[k] = 0;
+    }
+}
+
+TimedScope::TimedScope(int k, cudaStream_t s) : kind(k), level(g_timing_level), stream(s) {
     TimingState& t = timing();
     std::lock_guard<std::mutex> lk(t.mu);
     if (!t.on) return;
@@ -72,7 +111,7 @@ TimedScope::~TimedScope() {
     std::lock_guard<std::mutex> lk(t.mu);
     cudaEvent_t end = t.get();
     cudaEventRecord(end, stream);
-    t.pending.emplace_back(kind, start, end);
+    t.pending.emplace_back(kind, level, start, end);
 }
 
 namespace {
@@ -710,28 +749,7 @@ ifgf_status ifgf_release_cached_memory(void) {
 }
 
 ifgf_status ifgf_timing_collect(double* ms, int64_t* launches) {
-    TimingState& t = timing();
-    std::lock_guard<std::mutex> lk(t.mu);
-    ifgf_status st = IFGF_OK;
-    for (auto& [k, a, b] : t.pending) {
-        float el = 0.f;
-        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&el, a, b) != cudaSuccess) {
-            cudaGetLastError();
-            st = IFGF_ERR_CUDA;
-        }
-        t.ms[k] += el;
-        t.launches[k] += 1;
-        t.pool.push_back(a);
-        t.pool.push_back(b);
-    }
-    t.pending.clear();
-    for (int k = 0; k < TK_COUNT; ++k) {
-        if (ms) ms[k] = t.ms[k];
-        if (launches) launches[k] = t.launches[k];
-        t.ms[k] = 0;
-        t.launches[k] = 0;
-    }
-    return st;
+    return guard([&] { timing_collect_levels(ms, launches, nullptr); });
 }
 
 }  // extern "C"

@@ -7,10 +7,12 @@
 // The problems of the batch share the launch sequence, not their data: each plan keeps its
 // own tree, cones and scratch.
 #include <algorithm>
+#include <cstdio>
 #include <functional>
 #include <string>
 #include <vector>
 
+#include "batch_queue.cuh"
 #include "ifgf_internal.cuh"
 
 struct ifgf_plan_s;  // opaque handle of api.cu (derives from ifgf::Plan)
@@ -29,6 +31,14 @@ struct ifgf_batch_s {
     std::vector<void*> outs;
     std::vector<int32_t> nrhs;
     int64_t launches_per_replay = 0;
+    // queue mode (batch_queue.cu): -1 where eligible, 0 never, 1 always
+    int mode = -1;
+    int last_mode = -1;
+    ifgf::QueueConfig qc;
+    ifgf::BatchQueue* queue = nullptr;
+    cudaGraph_t qgraph = nullptr;
+    cudaGraphExec_t qexec = nullptr;
+    int64_t q_launches = 0;
 };
 
 namespace ifgf {
@@ -45,6 +55,12 @@ void drop_graph(ifgf_batch_s& b) {
     if (b.graph) cudaGraphDestroy(b.graph);
     b.exec = nullptr;
     b.graph = nullptr;
+}
+void drop_qgraph(ifgf_batch_s& b) {
+    if (b.qexec) cudaGraphExecDestroy(b.qexec);
+    if (b.qgraph) cudaGraphDestroy(b.qgraph);
+    b.qexec = nullptr;
+    b.qgraph = nullptr;
 }
 }  // namespace
 
@@ -117,8 +133,43 @@ ifgf_status ifgf_batch_apply(ifgf_batch b, const void* const* dens, const int32_
             return IFGF_ERR_INVALID_ARG;
         }
     }
+    std::string why;
+    const bool eligible = queue_eligible(b->plans, nrhs, &why);
+    if (b->mode == 1 && !eligible) {
+        set_last_error("queue mode: " + why);
+        return IFGF_ERR_UNSUPPORTED;
+    }
+    if (b->mode != 0 && eligible) {
+        return guard_call([&] {
+            IFGF_CUDA(cudaSetDevice(b->device));
+            if (!b->queue) b->queue = queue_create(b->plans);
+            queue_set_io(b->queue, dens, outs, (cudaStream_t)stream);
+            if (!b->qexec) {
+                queue_prepare(b->queue, b->qc);
+                const int64_t l0 = g_launches.load();
+                IFGF_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+                try {
+                    queue_record(b->queue, b->qc, b->cap);
+                } catch (...) {
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(b->cap, &g);
+                    if (g) cudaGraphDestroy(g);
+                    cudaGetLastError();
+                    throw;
+                }
+                IFGF_CUDA(cudaStreamEndCapture(b->cap, &b->qgraph));
+                IFGF_CUDA(cudaGraphInstantiate(&b->qexec, b->qgraph, 0));
+                b->q_launches = g_launches.load() - l0;
+                g_launches.fetch_sub(b->q_launches);  // counted when replayed
+            }
+            IFGF_CUDA(cudaGraphLaunch(b->qexec, (cudaStream_t)stream));
+            g_launches.fetch_add(b->q_launches);
+            b->last_mode = 1;
+        });
+    }
     return guard_call([&] {
         IFGF_CUDA(cudaSetDevice(b->device));
+        b->last_mode = 0;
         bool same = b->exec != nullptr && b->dens.size() == n;
         for (size_t i = 0; same && i < n; ++i)
             same = b->dens[i] == dens[i] && b->outs[i] == outs[i] && b->nrhs[i] == nrhs[i];
@@ -158,10 +209,156 @@ ifgf_status ifgf_batch_apply(ifgf_batch b, const void* const* dens, const int32_
     });
 }
 
+ifgf_status ifgf_batch_set(ifgf_batch b, int32_t what, int64_t value) {
+    if (!b) {
+        set_last_error("NULL batch");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    bool ok = true;
+    switch (what) {
+        case IFGF_BATCH_MODE:
+            ok = value >= -1 && value <= 1;
+            if (ok) b->mode = (int)value;
+            break;
+        case IFGF_BATCH_CONES_PER_ITEM:
+            ok = value >= 4 && value <= (1 << 20);
+            if (ok) b->qc.cones_per_item = (int)value;
+            break;
+        case IFGF_BATCH_BLOCKS_PER_SM:
+            ok = value >= 0 && value <= 64;
+            if (ok) b->qc.blocks_per_sm = (int)value;
+            break;
+        case IFGF_BATCH_WAIT_LIMIT:
+            ok = value >= 0;
+            if (ok) b->qc.wait_limit = value;
+            break;
+        case IFGF_BATCH_WITHHOLD:
+            if (value < 0) {
+                b->qc.withhold = -1;
+            } else {
+                const int64_t prob = value / 64, lev = value % 64;
+                ok = prob < (int64_t)b->plans.size() && lev >= 4 && lev <= b->plans[prob]->D;
+                if (ok) b->qc.withhold = (int)value;
+            }
+            break;
+        default:
+            ok = false;
+    }
+    if (!ok) {
+        set_last_error("unknown batch setting or value out of range");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    drop_qgraph(*b);  // the next queue apply records the sequence with the new settings
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_batch_get(ifgf_batch b, int32_t what, int64_t* value) {
+    if (!b || !value) {
+        set_last_error("NULL batch or value pointer");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    switch (what) {
+        case IFGF_BATCH_MODE: *value = b->mode; return IFGF_OK;
+        case IFGF_BATCH_CONES_PER_ITEM: *value = b->qc.cones_per_item; return IFGF_OK;
+        case IFGF_BATCH_BLOCKS_PER_SM: *value = b->qc.blocks_per_sm; return IFGF_OK;
+        case IFGF_BATCH_WAIT_LIMIT: *value = b->qc.wait_limit; return IFGF_OK;
+        case IFGF_BATCH_LAST_MODE: *value = b->last_mode; return IFGF_OK;
+        case IFGF_BATCH_ITEMS: *value = b->queue ? queue_items(b->queue) : 0; return IFGF_OK;
+        case IFGF_BATCH_STATUS:
+            if (!b->queue) {
+                *value = IFGF_OK;
+                return IFGF_OK;
+            }
+            return guard_call([&] { *value = queue_status(b->queue); });
+        default:
+            set_last_error("unknown batch query");
+            return IFGF_ERR_INVALID_ARG;
+    }
+}
+
+ifgf_status ifgf_batch_autotune(ifgf_batch b, const void* const* dens, const int32_t* nrhs, void* const* outs,
+                                const char* cache_path, void* stream, int32_t* from_cache) {
+    if (!b || !dens || !nrhs || !outs) {
+        set_last_error("NULL batch or buffer arrays");
+        return IFGF_ERR_INVALID_ARG;
+    }
+    if (from_cache) *from_cache = 1;
+    const bool eligible = queue_eligible(b->plans, nrhs, nullptr);
+    int64_t total = 0, largest = 0;
+    int rmax = 1;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        total += b->plans[i]->N;
+        largest = std::max<int64_t>(largest, b->plans[i]->N);
+        rmax = std::max<int>(rmax, nrhs[i]);
+    }
+    struct Cand {
+        int mode, cpi, bps;
+    };
+    std::vector<Cand> cands{{0, 16, 0}};
+    if (eligible)
+        for (int cpi : {8, 16, 32, 64})
+            for (int bps : {0, 2}) cands.push_back({1, cpi, bps});
+    Cand best = cands.back();
+    ifgf_status st = guard_call([&] {
+        IFGF_CUDA(cudaSetDevice(b->device));
+        const std::string key = "batch|" + tune_gpu_key(b->device) + "|n=" + std::to_string(tune_log2((int64_t)b->plans.size())) +
+                                "|N=" + std::to_string(tune_log2(total)) + "|M=" + std::to_string(tune_log2(largest)) +
+                                "|r=" + tune_rhs_bucket(rmax) + "|q=" + (eligible ? "1" : "0");
+        std::map<std::string, std::string> cache;
+        if (cache_path) cache = tune_cache_read(cache_path);
+        auto it = cache.find(key);
+        if (it != cache.end() && std::sscanf(it->second.c_str(), "%d,%d,%d", &best.mode, &best.cpi, &best.bps) == 3 &&
+            (best.mode == 0 || eligible))
+            return;
+        if (from_cache) *from_cache = 0;
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        IFGF_CUDA(cudaEventCreate(&e0));
+        IFGF_CUDA(cudaEventCreate(&e1));
+        double best_ms = 1e300;
+        for (const Cand& c : cands) {
+            b->mode = c.mode;
+            b->qc.cones_per_item = c.cpi;
+            b->qc.blocks_per_sm = c.bps;
+            drop_qgraph(*b);
+            ifgf_status r = ifgf_batch_apply(b, dens, nrhs, outs, stream);  // capture and warm-up
+            if (r != IFGF_OK) fail(r, "batch apply while tuning");
+            std::vector<double> ms;
+            for (int k = 0; k < 3; ++k) {
+                IFGF_CUDA(cudaEventRecord(e0, s));
+                r = ifgf_batch_apply(b, dens, nrhs, outs, stream);
+                if (r != IFGF_OK) fail(r, "batch apply while tuning");
+                IFGF_CUDA(cudaEventRecord(e1, s));
+                IFGF_CUDA(cudaEventSynchronize(e1));
+                float t = 0.f;
+                IFGF_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                ms.push_back(t);
+            }
+            std::sort(ms.begin(), ms.end());
+            if (ms[1] < best_ms) {
+                best_ms = ms[1];
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cache_path)
+            tune_cache_write(cache_path, {{key, std::to_string(best.mode) + "," + std::to_string(best.cpi) + "," +
+                                                    std::to_string(best.bps)}});
+    });
+    b->mode = best.mode;
+    b->qc.cones_per_item = best.cpi;
+    b->qc.blocks_per_sm = best.bps;
+    drop_qgraph(*b);
+    return st;
+}
+
 ifgf_status ifgf_batch_destroy(ifgf_batch b) {
     if (!b) return IFGF_OK;
     cudaSetDevice(b->device);
     drop_graph(*b);
+    drop_qgraph(*b);
+    ifgf::queue_destroy(b->queue);
     for (cudaStream_t x : b->branch) cudaStreamDestroy(x);
     for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);

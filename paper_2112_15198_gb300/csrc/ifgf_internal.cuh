@@ -16,6 +16,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -304,9 +305,29 @@ struct TimedScope {
     TimedScope(int kind, cudaStream_t s);
     ~TimedScope();
     int kind;
+    int level = -1;
     cudaStream_t stream;
     cudaEvent_t start = nullptr;
 };
+// Tags the timed scopes of the calling thread with an octree level while it lives (the level
+// sweeps set it, so that the autotuner can read kernel times per level).
+struct TimingLevel {
+    explicit TimingLevel(int d);
+    ~TimingLevel();
+    int prev;
+};
+// Kernel times collected since the last collection, in total per kind and per (kind, level);
+// clears them (ifgf_timing_collect reports the totals).
+void timing_collect_levels(double* ms, int64_t* launches, double (*by_level)[kMaxLevel + 1]);
+// Switches the kernel timing on or off and returns the previous setting.
+bool timing_switch(bool on);
+
+// ---- autotuner cache (tune.cu) ---------------------------------------------------------
+std::map<std::string, std::string> tune_cache_read(const std::string& path);
+void tune_cache_write(const std::string& path, const std::map<std::string, std::string>& add);
+std::string tune_gpu_key(int device);
+std::string tune_rhs_bucket(int nrhs);
+int tune_log2(int64_t n);
 
 // ---- scan / sort utilities (util.cu) --------------------------------------------------
 // Exclusive prefix sum of n int32 values into out (may alias in); returns nothing; the
@@ -538,11 +559,20 @@ __device__ __forceinline__ float2 row5(float2 c0, float2 c1, float2 c2, float2 c
     return bb;
 }
 
+// Loads of coefficients: through the non-coherent read-only path, or (kCoh) as ordinary cached
+// loads, for data that other blocks of the same launch wrote before this block's acquire (the
+// read-only path is reserved to data that no block writes during the launch).
+template <bool kCoh, class T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+    if constexpr (kCoh) return __ldca(p);
+    else return __ldg(p);
+}
+
 // Interpolant sum_abc c_abc T_a(ts) T_b(tt) T_c(tp), contracted phi, then theta, then s, with
 // packed FP32x2 FMAs (re and im share the real basis weight).  For P_phi = 5 two consecutive
 // rows (10 complex = 80 bytes, 16-byte aligned for an even row) are read with five 128-bit
 // loads; the coefficient block of a cone must be 16-byte aligned.
-template <int PS, int PT, int PP>
+template <int PS, int PT, int PP, bool kCoh = false>
 __device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float ts, float tt, float tp) {
     float Ts[PS], Tt[PT], Tp[PP];
     cheb_T<PS>(ts, Ts);
@@ -561,16 +591,16 @@ __device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float
         };
 #pragma unroll
         for (int m = 0; m < R / 2; ++m) {
-            const float4 v0 = __ldg(c4 + 5 * m + 0), v1 = __ldg(c4 + 5 * m + 1), v2 = __ldg(c4 + 5 * m + 2);
-            const float4 v3 = __ldg(c4 + 5 * m + 3), v4 = __ldg(c4 + 5 * m + 4);
+            const float4 v0 = ld_ro<kCoh>(c4 + 5 * m + 0), v1 = ld_ro<kCoh>(c4 + 5 * m + 1), v2 = ld_ro<kCoh>(c4 + 5 * m + 2);
+            const float4 v3 = ld_ro<kCoh>(c4 + 5 * m + 3), v4 = ld_ro<kCoh>(c4 + 5 * m + 4);
             fold(2 * m, row5(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
                              make_float2(v1.z, v1.w), make_float2(v2.x, v2.y), Tp));
             fold(2 * m + 1, row5(make_float2(v2.z, v2.w), make_float2(v3.x, v3.y), make_float2(v3.z, v3.w),
                                  make_float2(v4.x, v4.y), make_float2(v4.z, v4.w), Tp));
         }
         if constexpr (R % 2 == 1) {
-            const float4 v0 = __ldg(c4 + 5 * (R / 2) + 0), v1 = __ldg(c4 + 5 * (R / 2) + 1);
-            const float2 v2 = __ldg(c + 10 * (R / 2) + 4);
+            const float4 v0 = ld_ro<kCoh>(c4 + 5 * (R / 2) + 0), v1 = ld_ro<kCoh>(c4 + 5 * (R / 2) + 1);
+            const float2 v2 = ld_ro<kCoh>(c + 10 * (R / 2) + 4);
             fold(R - 1, row5(make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
                              make_float2(v1.z, v1.w), v2, Tp));
         }
@@ -588,7 +618,7 @@ __device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float
                 float2 bb = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int q = 0; q < PP; ++q) {
-                    const float2 co = __ldg(c + (a * PT + b) * PP + q);
+                    const float2 co = ld_ro<kCoh>(c + (a * PT + b) * PP + q);
                     bb = __ffma2_rn(co, make_float2(Tp[q], Tp[q]), bb);
                 }
                 aa = __ffma2_rn(bb, make_float2(Tt[b], Tt[b]), aa);
@@ -604,7 +634,7 @@ __device__ __forceinline__ float2 interp_f32(const float2* __restrict__ c, float
 // drop by R. Row (a, b) enters point q with weight T_a(ts_q) T_b(tt_q).
 // kShared: the coefficient block was staged in shared memory (same layout) and is read with
 // plain loads; otherwise it is read from global memory through the read-only path.
-template <int PS, int PT, int PP, int R, bool kShared = false>
+template <int PS, int PT, int PP, int R, bool kShared = false, bool kCoh = false>
 __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, const float* ts, const float* tt,
                                                const float* tp, float2* out) {
     float Ts[R][PS], Tt[R][PT], Tp[R][PP];
@@ -631,7 +661,7 @@ __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, con
         const float4* c4 = reinterpret_cast<const float4*>(c);
         auto ld4 = [&](int i) -> float4 {
             if constexpr (kShared) return c4[i];
-            else return __ldg(c4 + i);
+            else return ld_ro<kCoh>(c4 + i);
         };
 #pragma unroll
         for (int m = 0; m < NR / 2; ++m) {
@@ -648,7 +678,7 @@ __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, con
             const float4 v0 = ld4(5 * (NR / 2) + 0), v1 = ld4(5 * (NR / 2) + 1);
             float2 v2;
             if constexpr (kShared) v2 = c[10 * (NR / 2) + 4];
-            else v2 = __ldg(c + 10 * (NR / 2) + 4);
+            else v2 = ld_ro<kCoh>(c + 10 * (NR / 2) + 4);
             const float2 r0[5] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
                                   make_float2(v1.z, v1.w), v2};
             fold(NR - 1, r0);
@@ -660,7 +690,7 @@ __device__ __forceinline__ void interp_f32_seg(const float2* __restrict__ c, con
 #pragma unroll
             for (int k = 0; k < PP; ++k) {
                 if constexpr (kShared) row[k] = c[rr * PP + k];
-                else row[k] = __ldg(c + rr * PP + k);
+                else row[k] = ld_ro<kCoh>(c + rr * PP + k);
             }
             // rr is not a compile-time constant here: weights by explicit selection
             const int a = rr / PT, b = rr - (rr / PT) * PT;

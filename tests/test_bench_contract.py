@@ -64,9 +64,12 @@ def test_traffic_record_is_keyed_by_the_kernel_source():
     csrc = os.path.join(ROOT, "paper_2112_15198_gb300", "csrc")
     apply_src = open(os.path.join(csrc, "apply.cu")).read()
     header = open(os.path.join(csrc, "ifgf_internal.cuh")).read()
-    sha = bench.kernel_source_sha("k_prop_warp_f32", apply_src, header)
-    assert sha == bench.kernel_source_sha("k_prop_warp_f32", apply_src + "\n// trailing\n", header)
-    assert sha != bench.kernel_source_sha("k_prop_warp_f32", apply_src.replace("kSegLen / 2", "kSegLen/2"), header)
+    bodies = open(os.path.join(csrc, "bodies_f32.cuh")).read()
+    sha = bench.kernel_source_sha("k_prop_warp_f32", apply_src, header, bodies)
+    assert sha == bench.kernel_source_sha("k_prop_warp_f32", apply_src + "\n// trailing\n", header, bodies)
+    assert sha != bench.kernel_source_sha("k_prop_warp_f32", apply_src, header, bodies.replace("kSegLen / 2", "kSegLen/2"))
+    assert sha != bench.kernel_source_sha("k_prop_warp_f32", apply_src.replace("kWarpCones + warp", "kWarpCones+warp"),
+                                          header, bodies)
     recorded = [ln for ln in open(os.path.join(ROOT, "profiles", "traffic.txt")) if ln.startswith("kernel=")]
     assert recorded and all("source_sha=" in ln for ln in recorded)
 
