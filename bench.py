@@ -76,9 +76,11 @@ def parse():
     ap.add_argument("--workload", default="sphere512")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--study", default="", choices=["", "linearithmic"],
+    ap.add_argument("--study", default="", choices=["", "linearithmic", "batch"],
                     help="linearithmic: plan + apply time and error against N log N for four sizes of the "
-                         "sphere and the prolate spheroid (fixed sampling density)")
+                         "sphere and the prolate spheroid (fixed sampling density); batch: the 64-problem uneven batch (spheres and spheroids of 2-32 wavelengths), one batched "
+                         "apply per step: sequential applies, the per-plan graph sequence and the queue "
+                         "sequence, and the autotuner's choice")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the FP64 GPU and kappa = 0 records beside the line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -495,6 +497,80 @@ def run_linearithmic(args):
                       "rows": rows}), flush=True)
 
 
+def run_batch(args):
+    """The uneven batch (64 spheres and (a, a, a/2) spheroids, 2-32 wavelengths, N from 6,144 to
+    264,192 at about 100 points per square wavelength, one density each): plans and batch built
+    once outside the timed region, then per step one batched apply (CUDA events, L2 flushed,
+    mean over the timed steps after the warm-up): the plans' applies one after another, the
+    per-plan graph sequence, the queue sequence at the autotuner's split, and the sequence the
+    autotuner chose (cached in the build folder).  Error per problem on 100 seeded targets against
+    the direct sum; every problem's batched result is checked bit-identical to its own apply."""
+    import torch
+
+    import oracle
+    import paper_2112_15198_gb300 as ifgf
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    probs = W.batch_problems()
+    pts = [w.points() for w in probs]
+    dens_h = [w.densities() for w in probs]
+    P = [torch.from_numpy(x).to(dev) for x in pts]
+    dens = [torch.from_numpy(d).to(dev).to(torch.complex64) for d in dens_h]
+    outs = [torch.empty_like(d) for d in dens]
+    ref = [torch.empty_like(d) for d in dens]
+    t0 = time.perf_counter()
+    plans = [ifgf.Plan(x, w.kappa) for x, w in zip(P, probs)]
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    ntot = sum(w.n for w in probs)
+
+    def singles(o):
+        for p_, d_, x_ in zip(plans, dens, o):
+            p_.apply(d_, x_)
+
+    singles(ref)
+    batch = ifgf.Batch(plans)
+    cache = os.path.join(ROOT, "paper_2112_15198_gb300", "_build", "tune_cache.txt")
+    hit = batch.autotune(dens, outs, cache_path=cache)
+    mode, cpi = batch.get(ifgf.BATCH.MODE), batch.get(ifgf.BATCH.CONES_PER_ITEM)
+    bps = batch.get(ifgf.BATCH.BLOCKS_PER_SM)
+    res = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, m in (("sequential", None), ("graph", 0), ("queue", 1), ("tuned", mode)):
+        if m is None:
+            fn = lambda: singles(outs)  # noqa: E731
+        else:
+            batch.set(ifgf.BATCH.MODE, m)
+            fn = lambda: batch.apply(dens, outs)  # noqa: E731
+        for _ in range(max(3, args.warmup)):
+            fn()
+        ms = statistics.mean(timed_steps(torch, stream, flush, fn, max(1, args.steps)))
+        torch.cuda.synchronize()
+        same = all(torch.equal(o, r) for o, r in zip(outs, ref))
+        res[name] = {"ms_per_step": ms, "pts_per_s": ntot / (ms * 1e-3), "bit_identical_to_own_apply": same}
+    ck = clocks.stop()
+    worst = 0.0
+    for w, x, d, o in zip(probs, pts, dens_h, ref):
+        tg = w.targets()[:100]
+        worst = max(worst, rel_l2(o.cpu().numpy().astype(np.complex128)[:, tg], oracle.direct_sum(x, w.kappa, d, tg)))
+    print(json.dumps({"study": "batch", "metric": "IFGF matvecs/sec (N*nrhs pts/s) at stated rel. error vs FP64 "
+                      "direct sum", "unit": "pts/s", "value": res["tuned"]["pts_per_s"],
+                      "ms_per_step": res["tuned"]["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "batch64 (64 problems, 6,144-264,192 points each)", "points": ntot,
+                                 "problems": len(probs), "nrhs": 1, "step": "one batched apply (plans built once)",
+                                 "l2": "flushed before each step", "plans_s": plan_s,
+                                 "tuned": {"mode": "queue" if mode == 1 else "graph", "cones_per_item": cpi,
+                                           "blocks_per_sm": bps, "from_cache": hit}},
+                      "sequences": res, "worst_rel_err": worst, "targets_per_problem": 100,
+                      "batch_status": batch.get(ifgf.BATCH.STATUS), "clocks": ck}), flush=True)
+    batch.destroy()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -504,6 +580,10 @@ def main():
     if args.study == "linearithmic":
         if rank == 0:
             run_linearithmic(args)
+        return
+    if args.study == "batch":
+        if rank == 0:
+            run_batch(args)
         return
     import torch
 

@@ -202,13 +202,16 @@ typedef enum {
  * the plan's own ifgf_apply.  Two launch sequences are built:
  *   queue  (plans of mixed precision with orders (3,5,5), one density each) one short sequence
  *          over work lists that mix all problems, largest first: permutation in, near field,
- *          LevelDEvaluations (Algorithm 6), one persistent propagation kernel (Algorithm 7) for
- *          every level of every problem, interpolation (Algorithm 8) and permutation out.  The
- *          propagation's blocks take runs of parent cones from a queue ordered by the distance of
- *          the child level from the problem's leaves; a run whose child level is not complete
- *          waits on the problem's per-level counter (waits bounded by IFGF_BATCH_WAIT_LIMIT
- *          polls, see ifgf_batch_set).  It keeps the coefficients of every level of every
- *          problem (device memory owned by the batch, allocated at the first queue apply).
+ *          LevelDEvaluations (Algorithm 6), the propagation (Algorithm 7), interpolation
+ *          (Algorithm 8, one level per work unit) and permutation out with the level sums added
+ *          in the single-plan order.  The propagation is either a persistent kernel per run of
+ *          levels of one kind, whose blocks take runs of parent cones from a queue ordered by the
+ *          distance of the child level from the problem's leaves (a run whose child level is not
+ *          complete waits on the problem's per-level counter; waits bounded by
+ *          IFGF_BATCH_WAIT_LIMIT polls, see ifgf_batch_set), or each plan's own per-level kernels
+ *          on concurrent branches.  It keeps the coefficients and interpolation sums of every
+ *          level of every problem (device memory owned by the batch, allocated at the first
+ *          queue apply).
  *   graph  (any plans) each plan's own apply captured on branch i mod 8 of a fork/join, so that
  *          independent problems run concurrently.
  * Either sequence is captured into a CUDA graph by the first ifgf_batch_apply and replayed with
@@ -225,9 +228,10 @@ typedef enum {
  *   outs   n device pointers, plan i's outputs.
  *
  * ifgf_batch_set / ifgf_batch_get (host; a change takes effect at the next apply):
- *   IFGF_BATCH_MODE            -1 queue where the plans allow it, else graph (default); 0 graph;
- *                              1 queue (ifgf_batch_apply returns IFGF_ERR_UNSUPPORTED when the
- *                              plans do not allow it).
+ *   IFGF_BATCH_MODE            -1 (default) as 2 where the plans allow the queue, else 0;
+ *                              0 graph; 1 queue with the persistent propagation; 2 queue with
+ *                              each plan's propagation on branches (1 and 2: ifgf_batch_apply
+ *                              returns IFGF_ERR_UNSUPPORTED when the plans do not allow them).
  *   IFGF_BATCH_CONES_PER_ITEM  parent cones per propagation queue item, >= 4 (rounded down to a
  *                              multiple of 4; default 16).
  *   IFGF_BATCH_BLOCKS_PER_SM   resident blocks per SM of the persistent propagation (0: as many
@@ -241,8 +245,8 @@ typedef enum {
  *                              limit; -1 turns it off.
  *   get only: IFGF_BATCH_STATUS (synchronises the device; the status word of the last queue
  *   sequence, IFGF_OK or IFGF_ERR_TIMEOUT, reset by every queue apply), IFGF_BATCH_LAST_MODE (the
- *   sequence the last apply ran: 0 graph, 1 queue, -1 none), IFGF_BATCH_ITEMS (propagation
- *   queue items of the last queue sequence).
+ *   sequence the last apply ran: 0, 1 or 2 as IFGF_BATCH_MODE, -1 none), IFGF_BATCH_ITEMS
+ *   (propagation queue items of the last queue sequence).
  * Errors: IFGF_ERR_INVALID_ARG for a NULL handle or pointer, an unknown code or a value out of
  * range.
  */
@@ -255,8 +259,9 @@ ifgf_status ifgf_batch_get(ifgf_batch batch, int32_t what, int64_t* value);
 
 /*
  * Autotuner of a batch: times ifgf_batch_apply with the given buffers (three replays after a
- * warm-up) for the graph sequence and, where the plans allow it, the queue sequence with 8, 16,
- * 32 and 64 parent cones per item and 0 or 2 blocks per SM; sets the fastest (IFGF_BATCH_MODE,
+ * warm-up) for the graph sequence and, where the plans allow it, the queue sequence with branch
+ * propagation and with the persistent propagation at 8, 16, 32 and 64 parent cones per item and
+ * 0 or 2 blocks per SM; sets the fastest (IFGF_BATCH_MODE,
  * IFGF_BATCH_CONES_PER_ITEM, IFGF_BATCH_BLOCKS_PER_SM).  Choices are cached in cache_path (NULL:
  * no cache) under a key of the GPU, the number of problems, their total and largest N (floor
  * log2 each), the densities bucket and whether the queue applies; with a cache hit nothing is
@@ -339,6 +344,32 @@ ifgf_status ifgf_plan_get_knob(ifgf_plan plan, int32_t knob, int32_t level, int3
  */
 ifgf_status ifgf_plan_autotune(ifgf_plan plan, int32_t nrhs, const char* cache_path, void* stream,
                                int32_t* from_cache);
+
+/*
+ * Solver integration: restarted GMRES(restart) for the second-kind system
+ *     (alpha I + beta A W) x = b,
+ * A the plan's operator of Eq. (1) (one ifgf_apply per iteration, the plan's precision) and W the
+ * diagonal of the quadrature weights.  This is the use of the apply that the paper's Sec. 1-2
+ * describe (the matrix-vector product of an iterative solver for a boundary integral equation);
+ * the near field stays the point sum of Eq. (1): singular quadratures are not part of the paper.
+ * Arnoldi with classical Gram-Schmidt applied twice; inner products accumulated in FP64 in a
+ * fixed order (a solve is reproducible); Givens least squares on the host.
+ *
+ *   b, x         device, N complex values in the caller's point order (complex64 on a mixed plan,
+ *                complex128 on an FP64 plan); x holds the initial guess and receives the solution.
+ *   alpha, beta  host, 2 doubles each (real, imaginary part).
+ *   weights      device, N reals (float32 mixed / float64 FP64) or NULL (all ones).
+ *   restart      Krylov dimension per cycle, 1..128;  max_iters >= 1 (applies of A, not counting
+ *                one per restart for the residual);  tol > 0: stop when |b - (alpha + beta A W) x|
+ *                <= tol |b| (GMRES's estimate; the final residual is recomputed).
+ *   iters, rel_residual  optional host outputs: iterations done, final relative residual.
+ * Synchronous on `stream` (the host reads inner products every iteration).  Scratch: restart + 4
+ * vectors of N from the library's pool.  Errors: IFGF_ERR_INVALID_ARG (NULL or aliased
+ * pointers, parameters out of range), IFGF_ERR_OOM, IFGF_ERR_CUDA.
+ */
+ifgf_status ifgf_gmres(ifgf_plan plan, const void* b, void* x, const double* alpha, const double* beta,
+                       const void* weights, int32_t restart, int32_t max_iters, double tol, void* stream,
+                       int32_t* iters, double* rel_residual);
 
 /*
  * Distribution over several GPUs (Sec. 3.2), one rank per GPU.

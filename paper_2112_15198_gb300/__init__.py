@@ -163,6 +163,9 @@ def load(build: bool = True):
         lib.ifgf_plan_set_knob.restype = ctypes.c_int
         lib.ifgf_plan_get_knob.argtypes = [vp, i32, i32, ctypes.POINTER(i32)]
         lib.ifgf_plan_get_knob.restype = ctypes.c_int
+        lib.ifgf_gmres.argtypes = [vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp, i32, i32, dbl, vp,
+                                   ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+        lib.ifgf_gmres.restype = ctypes.c_int
         lib.ifgf_permute.argtypes = [vp, vp, i32, vp, i32, vp]
         lib.ifgf_permute.restype = ctypes.c_int
         lib.ifgf_timing_enable.argtypes = [i32]
@@ -428,6 +431,19 @@ class Plan:
         """Kernel choice of the apply (ifgf_plan_set_knob): KNOB.PROP_MANY / KNOB.PROP_FEW per level
         d of the propagation from d into d-1, KNOB.RHS_BLOCK plan-wide; -1 restores the built-in."""
         _check(self._lib.ifgf_plan_set_knob(self._h, int(knob), int(level), int(value)))
+
+    def gmres(self, b, x, alpha=1.0, beta=1.0, weights=None, restart: int = 30, max_iters: int = 200,
+              tol: float = 1e-4, stream=None):
+        """Solve (alpha I + beta A W) x = b by restarted GMRES with this plan's apply as A
+        (ifgf_gmres); x holds the initial guess and receives the solution.  Returns
+        (iterations, final relative residual)."""
+        a = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+        bt = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+        it = ctypes.c_int32(0)
+        res = ctypes.c_double(0.0)
+        _check(self._lib.ifgf_gmres(self._h, _ptr(b), _ptr(x), a, bt, _ptr(weights), int(restart), int(max_iters),
+                                    float(tol), _stream(stream), ctypes.byref(it), ctypes.byref(res)))
+        return int(it.value), float(res.value)
 
     def autotune(self, nrhs: int = 1, cache_path=None, stream=None) -> bool:
         """Times the kernel choices of an apply with nrhs densities and keeps the fastest

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, f"libifgf_{platform.machine()}.so")
 # the same sources with every bounds check compiled in (-DIFGF_CHECKS)
 CHECKS_LIB = os.path.join(BUILD, f"libifgf_checks_{platform.machine()}.so")
-SOURCES = ["util.cu", "plan.cu", "apply.cu", "api.cu", "noalloc.cu", "batch.cu", "batch_queue.cu", "shard.cu", "prop_tc.cu", "tune.cu"]
+SOURCES = ["util.cu", "plan.cu", "apply.cu", "api.cu", "noalloc.cu", "batch.cu", "batch_queue.cu", "shard.cu", "prop_tc.cu", "tune.cu", "solve.cu"]
 # throughput probes for the roofline denominators (a library of their own)
 PEAKS_LIB = os.path.join(BUILD, f"libifgf_peaks_{platform.machine()}.so")
 PEAKS_SOURCES = ["peaks.cu"]

@@ -32,7 +32,7 @@ struct ifgf_batch_s {
     std::vector<int32_t> nrhs;
     int64_t launches_per_replay = 0;
     // queue mode (batch_queue.cu): -1 where eligible, 0 never, 1 always
-    int mode = -1;
+    int mode = -1;                  // 2: queue sequence with each plan's propagation on branches
     int last_mode = -1;
     ifgf::QueueConfig qc;
     ifgf::BatchQueue* queue = nullptr;
@@ -135,11 +135,13 @@ ifgf_status ifgf_batch_apply(ifgf_batch b, const void* const* dens, const int32_
     }
     std::string why;
     const bool eligible = queue_eligible(b->plans, nrhs, &why);
-    if (b->mode == 1 && !eligible) {
+    if ((b->mode == 1 || b->mode == 2) && !eligible) {
         set_last_error("queue mode: " + why);
         return IFGF_ERR_UNSUPPORTED;
     }
-    if (b->mode != 0 && eligible) {
+    // -1: the queue sequence with each plan's propagation on branches where the plans allow it
+    const int eff = b->mode == -1 ? (eligible ? 2 : 0) : b->mode;
+    if (eff != 0) {
         return guard_call([&] {
             IFGF_CUDA(cudaSetDevice(b->device));
             if (!b->queue) b->queue = queue_create(b->plans);
@@ -149,7 +151,10 @@ ifgf_status ifgf_batch_apply(ifgf_batch b, const void* const* dens, const int32_
                 const int64_t l0 = g_launches.load();
                 IFGF_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
                 try {
-                    queue_record(b->queue, b->qc, b->cap);
+                    if (eff == 2)
+                        queue_record(b->queue, b->qc, b->cap, &b->branch, &b->ev);
+                    else
+                        queue_record(b->queue, b->qc, b->cap);
                 } catch (...) {
                     cudaGraph_t g = nullptr;
                     cudaStreamEndCapture(b->cap, &g);
@@ -164,7 +169,7 @@ ifgf_status ifgf_batch_apply(ifgf_batch b, const void* const* dens, const int32_
             }
             IFGF_CUDA(cudaGraphLaunch(b->qexec, (cudaStream_t)stream));
             g_launches.fetch_add(b->q_launches);
-            b->last_mode = 1;
+            b->last_mode = eff;
         });
     }
     return guard_call([&] {
@@ -217,7 +222,7 @@ ifgf_status ifgf_batch_set(ifgf_batch b, int32_t what, int64_t value) {
     bool ok = true;
     switch (what) {
         case IFGF_BATCH_MODE:
-            ok = value >= -1 && value <= 1;
+            ok = value >= -1 && value <= 2;
             if (ok) b->mode = (int)value;
             break;
         case IFGF_BATCH_CONES_PER_ITEM:
@@ -295,9 +300,11 @@ ifgf_status ifgf_batch_autotune(ifgf_batch b, const void* const* dens, const int
         int mode, cpi, bps;
     };
     std::vector<Cand> cands{{0, 16, 0}};
-    if (eligible)
+    if (eligible) {
+        cands.push_back({2, 16, 0});
         for (int cpi : {8, 16, 32, 64})
             for (int bps : {0, 2}) cands.push_back({1, cpi, bps});
+    }
     Cand best = cands.back();
     ifgf_status st = guard_call([&] {
         IFGF_CUDA(cudaSetDevice(b->device));

@@ -503,7 +503,8 @@ void queue_prepare(BatchQueue* q, const QueueConfig& c) {
     }
 }
 
-void queue_record(BatchQueue* q, const QueueConfig& c, cudaStream_t s) {
+void queue_record(BatchQueue* q, const QueueConfig& c, cudaStream_t s, const std::vector<cudaStream_t>* branches,
+                  const std::vector<cudaEvent_t>* ev) {
     BatchQueue& Q = *q;
     if (Q.cones_per_item != std::max(4, c.cones_per_item / 4 * 4))
         fail(IFGF_ERR_INTERNAL, "queue recorded before its items were built");
@@ -518,7 +519,25 @@ void queue_record(BatchQueue* q, const QueueConfig& c, cudaStream_t s) {
     int* bstatus = Q.dctr;
     int* heads = Q.dctr + 1;
     int* done = Q.dctr + 1 + kMaxPhases;
-    for (size_t ph = 0; ph + 1 < Q.phase_begin.size(); ++ph) {
+    if (branches && !branches->empty()) {
+        // each plan's own propagation kernels, problems spread over concurrent branches
+        const size_t kb = branches->size();
+        IFGF_CUDA(cudaEventRecord((*ev)[0], s));
+        for (size_t j = 0; j < kb; ++j) IFGF_CUDA(cudaStreamWaitEvent((*branches)[j], (*ev)[0], 0));
+        for (size_t i = 0; i < n; ++i) {
+            Plan& p = *Q.plans[i];
+            const QProblem& P = Q.hp[i];
+            for (int d = p.D; d >= 4; --d) {
+                const QLevel& L = Q.hl[P.lv0 + d - 3];
+                if (L.ncp > 0) shard_prop(p, d, 1, 0, L.ncp, L.cm, L.coef, L.cparent, (*branches)[i % kb]);
+            }
+        }
+        for (size_t j = 0; j < kb; ++j) {
+            IFGF_CUDA(cudaEventRecord((*ev)[j + 1], (*branches)[j]));
+            IFGF_CUDA(cudaStreamWaitEvent(s, (*ev)[j + 1], 0));
+        }
+    }
+    for (size_t ph = 0; !(branches && !branches->empty()) && ph + 1 < Q.phase_begin.size(); ++ph) {
         const int i0 = Q.phase_begin[ph], n = Q.phase_begin[ph + 1] - i0;
         if (n <= 0) continue;
         const int w = wh >= i0 && wh < i0 + n ? wh - i0 : -1;

@@ -31,8 +31,11 @@ void queue_set_io(BatchQueue* q, const void* const* dens, void* const* outs, cud
 // outside a stream capture).
 void queue_prepare(BatchQueue* q, const QueueConfig& c);
 // Enqueues the whole sequence on s (stream capture or direct): counter reset, permutation in,
-// near field, LevelDEvaluations, the persistent propagation, interpolation, permutation out.
-void queue_record(BatchQueue* q, const QueueConfig& c, cudaStream_t s);
+// near field, LevelDEvaluations, the propagation, interpolation, permutation out.  With branch
+// streams (fork/join events ev: one fork, then one per branch) the propagation is each plan's own
+// per-level kernels, plan i on branch i mod branches.size(), instead of the persistent queue.
+void queue_record(BatchQueue* q, const QueueConfig& c, cudaStream_t s, const std::vector<cudaStream_t>* branches = nullptr,
+                  const std::vector<cudaEvent_t>* ev = nullptr);
 // Queue items of the propagation (for tests and the withhold index) and the first item of a
 // (problem, level) pair, -1 if that level has no propagation.
 int64_t queue_items(const BatchQueue* q);

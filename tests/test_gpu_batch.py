@@ -41,7 +41,7 @@ def _singles(plans, dens):
     return out
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_small_batch_equals_single_plans_and_replays(mode):
     problems = W.batch_problems(count=6, seed=17)
     plans, dens, outs, host = _setup(problems)
@@ -163,7 +163,7 @@ def test_batch64_uneven_workload():
     batch.apply(dens, outs)
     batch.apply(dens, outs)
     torch.cuda.synchronize()
-    assert batch.get(ifgf.BATCH.LAST_MODE) == 1 and batch.get(ifgf.BATCH.STATUS) == 0
+    assert batch.get(ifgf.BATCH.LAST_MODE) == 2 and batch.get(ifgf.BATCH.STATUS) == 0
     for o, r in zip(outs, ref):
         assert torch.equal(o, r)
     worst = 0.0

@@ -76,7 +76,7 @@ def test_batch_autotune_keeps_results_and_caches(tmp_path):
     batch = ifgf.Batch(plans)
     assert batch.autotune(dens, outs, cache) is False
     mode = batch.get(ifgf.BATCH.MODE)
-    assert mode in (0, 1)
+    assert mode in (0, 1, 2)
     for o, r in zip(outs, refs):
         assert torch.equal(o, r)
     batch.apply(dens, outs)
