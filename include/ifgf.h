@@ -228,10 +228,10 @@ typedef enum {
  *   outs   n device pointers, plan i's outputs.
  *
  * ifgf_batch_set / ifgf_batch_get (host; a change takes effect at the next apply):
- *   IFGF_BATCH_MODE            -1 (default) as 2 where the plans allow the queue, else 0;
- *                              0 graph; 1 queue with the persistent propagation; 2 queue with
- *                              each plan's propagation on branches (1 and 2: ifgf_batch_apply
- *                              returns IFGF_ERR_UNSUPPORTED when the plans do not allow them).
+ *   IFGF_BATCH_MODE            -1 (default) the built-in choice, the graph sequence; 0 graph;
+ *                              1 queue with the persistent propagation; 2 queue with each plan's
+ *                              propagation on branches (1 and 2: ifgf_batch_apply returns
+ *                              IFGF_ERR_UNSUPPORTED when the plans do not allow them).
  *   IFGF_BATCH_CONES_PER_ITEM  parent cones per propagation queue item, >= 4 (rounded down to a
  *                              multiple of 4; default 16).
  *   IFGF_BATCH_BLOCKS_PER_SM   resident blocks per SM of the persistent propagation (0: as many

@@ -139,8 +139,9 @@ ifgf_status ifgf_batch_apply(ifgf_batch b, const void* const* dens, const int32_
         set_last_error("queue mode: " + why);
         return IFGF_ERR_UNSUPPORTED;
     }
-    // -1: the queue sequence with each plan's propagation on branches where the plans allow it
-    const int eff = b->mode == -1 ? (eligible ? 2 : 0) : b->mode;
+    // -1: the built-in choice, the graph sequence (fastest on the uneven 64-problem batch measured;
+    // ifgf_batch_autotune chooses per batch)
+    const int eff = b->mode == -1 ? 0 : b->mode;
     if (eff != 0) {
         return guard_call([&] {
             IFGF_CUDA(cudaSetDevice(b->device));

@@ -160,12 +160,16 @@ def test_batch64_uneven_workload():
     plans, dens, outs, host = _setup(problems)
     ref = _singles(plans, dens)
     batch = ifgf.Batch(plans)
-    batch.apply(dens, outs)
-    batch.apply(dens, outs)
-    torch.cuda.synchronize()
-    assert batch.get(ifgf.BATCH.LAST_MODE) == 2 and batch.get(ifgf.BATCH.STATUS) == 0
-    for o, r in zip(outs, ref):
-        assert torch.equal(o, r)
+    for mode in (0, 1, 2):
+        batch.set(ifgf.BATCH.MODE, mode)
+        for o in outs:
+            o.zero_()
+        batch.apply(dens, outs)
+        batch.apply(dens, outs)
+        torch.cuda.synchronize()
+        assert batch.get(ifgf.BATCH.LAST_MODE) == mode and batch.get(ifgf.BATCH.STATUS) == 0
+        for o, r in zip(outs, ref):
+            assert torch.equal(o, r)
     worst = 0.0
     for w, (pts, d), o in zip(problems, host, outs):
         tg = w.targets()
