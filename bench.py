@@ -81,6 +81,9 @@ def parse():
                          "sphere and the prolate spheroid (fixed sampling density); batch: the 64-problem uneven batch (spheres and spheroids of 2-32 wavelengths), one batched "
                          "apply per step: sequential applies, the per-plan graph sequence and the queue "
                          "sequence, and the autotuner's choice")
+    ap.add_argument("--batch-mode", type=int, default=-2, choices=[-2, 0, 1, 2],
+                    help="--study batch: -2 the autotuner's choice (default), else the batch sequence to time alone "
+                         "(0 graph, 1 queue with the persistent propagation, 2 queue with branch propagation)")
     ap.add_argument("--no-side", action="store_true",
                     help="skip the FP64 GPU and kappa = 0 records beside the line")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -533,14 +536,20 @@ def run_batch(args):
 
     singles(ref)
     batch = ifgf.Batch(plans)
-    cache = os.path.join(ROOT, "paper_2112_15198_gb300", "_build", "tune_cache.txt")
-    hit = batch.autotune(dens, outs, cache_path=cache)
+    if args.batch_mode == -2:
+        cache = os.path.join(ROOT, "paper_2112_15198_gb300", "_build", "tune_cache.txt")
+        hit = batch.autotune(dens, outs, cache_path=cache)
+        runs = (("sequential", None), ("graph", 0), ("queue_branches", 2), ("queue_persistent", 1))
+    else:
+        hit = None
+        batch.set(ifgf.BATCH.MODE, args.batch_mode)
+        runs = ()
     mode, cpi = batch.get(ifgf.BATCH.MODE), batch.get(ifgf.BATCH.CONES_PER_ITEM)
     bps = batch.get(ifgf.BATCH.BLOCKS_PER_SM)
     res = {}
     clocks = ClockSampler(0)
     clocks.start()
-    for name, m in (("sequential", None), ("graph", 0), ("queue", 1), ("tuned", mode)):
+    for name, m in runs + (("chosen", mode),):
         if m is None:
             fn = lambda: singles(outs)  # noqa: E731
         else:
@@ -558,14 +567,15 @@ def run_batch(args):
         tg = w.targets()[:100]
         worst = max(worst, rel_l2(o.cpu().numpy().astype(np.complex128)[:, tg], oracle.direct_sum(x, w.kappa, d, tg)))
     print(json.dumps({"study": "batch", "metric": "IFGF matvecs/sec (N*nrhs pts/s) at stated rel. error vs FP64 "
-                      "direct sum", "unit": "pts/s", "value": res["tuned"]["pts_per_s"],
-                      "ms_per_step": res["tuned"]["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
+                      "direct sum", "unit": "pts/s", "value": res["chosen"]["pts_per_s"],
+                      "ms_per_step": res["chosen"]["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "batch64 (64 problems, 6,144-264,192 points each)", "points": ntot,
                                  "problems": len(probs), "nrhs": 1, "step": "one batched apply (plans built once)",
                                  "l2": "flushed before each step", "plans_s": plan_s,
-                                 "tuned": {"mode": "queue" if mode == 1 else "graph", "cones_per_item": cpi,
-                                           "blocks_per_sm": bps, "from_cache": hit}},
+                                 "chosen": {"mode": {0: "graph", 1: "queue, persistent propagation",
+                                                     2: "queue, branch propagation"}[mode], "cones_per_item": cpi,
+                                            "blocks_per_sm": bps, "from_cache": hit}},
                       "sequences": res, "worst_rel_err": worst, "targets_per_problem": 100,
                       "batch_status": batch.get(ifgf.BATCH.STATUS), "clocks": ck}), flush=True)
     batch.destroy()

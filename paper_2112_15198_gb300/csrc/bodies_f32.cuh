@@ -360,7 +360,7 @@ __device__ __forceinline__ void prop_cones_f32(PropSmem<PS * PT * PP>& sm, int64
 // synchronising only itself.
 constexpr int kWarpCones = 2;  // warps (parent cones) per block
 constexpr int kWarpStage = 8; // child-cone coefficient blocks staged in shared memory per warp
-constexpr int kStage4 = 39;    // float4 per staged block (38 used; odd, so lanes reading different
+constexpr int kStage4 = 39;    // float4 per staged block (38 used at P = 75; odd, so lanes reading different
                                // blocks at one offset hit different banks)
 // NSETS = 1: one value set (grid row y = 0); NSETS = 0: all nrhs sets in turn, sharing the rows,
 // list entries and child-cone slots resolved once per warp.
@@ -464,8 +464,10 @@ __device__ __forceinline__ void prop_cone_warp_f32(WS* wp, int64_t ncp, const in
     const float* Wp = Wt + PT * PT;
     const int nsets = NSETS ? NSETS : nrhs;
     for (int r = 0; r < nsets; ++r) {
-    for (int x = lane; x < nst * 38; x += 32) {
-        const int j = x / 38, q = x - (x / 38) * 38;
+    constexpr int Q4 = (P + 1) / 2;  // float4 of a coefficient block (P complex values, cstride even)
+    static_assert(Q4 <= kStage4, "a staged coefficient block must fit its shared-memory slot");
+    for (int x = lane; x < nst * Q4; x += 32) {
+        const int j = x / Q4, q = x - (x / Q4) * Q4;
         const int sl = s_dsl[j];
         if (sl < 0) continue;  // missing cone: reported where it is used
         const float4* src = reinterpret_cast<const float4*>(cchild + ((int64_t)sl * nrhs + r) * cstride) + q;

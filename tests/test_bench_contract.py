@@ -68,7 +68,7 @@ def test_traffic_record_is_keyed_by_the_kernel_source():
     sha = bench.kernel_source_sha("k_prop_warp_f32", apply_src, header, bodies)
     assert sha == bench.kernel_source_sha("k_prop_warp_f32", apply_src + "\n// trailing\n", header, bodies)
     assert sha != bench.kernel_source_sha("k_prop_warp_f32", apply_src, header, bodies.replace("kSegLen / 2", "kSegLen/2"))
-    assert sha != bench.kernel_source_sha("k_prop_warp_f32", apply_src.replace("kWarpCones + warp", "kWarpCones+warp"),
+    assert sha != bench.kernel_source_sha("k_prop_warp_f32", apply_src.replace("kWarpCones + (threadIdx.x >> 5)", "kWarpCones+(threadIdx.x >> 5)"),
                                           header, bodies)
     recorded = [ln for ln in open(os.path.join(ROOT, "profiles", "traffic.txt")) if ln.startswith("kernel=")]
     assert recorded and all("source_sha=" in ln for ln in recorded)
