@@ -839,11 +839,12 @@ void build_node_tables(Plan& p, int dp) {
     // bytes: 30 per entry (coordinates, ratio, node, segment), lists and runs per row
     const int64_t bytes = entries * 30 + (int64_t)n_gam * 8 * (2 * kTabList + 3) * 4;
     // Tables of up to 1 GiB pay off from a sharing of 4; a level whose cone indices are each shared
-    // by 64 cones or more may take up to 48 GiB (and at most a quarter of the free device memory):
-    // on the 512-wavelength sphere the 38 GB tables of level 6 (sharing 128) save more time in the
-    // propagation and in the marking of relevant cones than they take to build.
+    // by 16 cones or more may take up to 48 GiB (and at most a quarter of the free device memory):
+    // on the 512-wavelength sphere the 38 GB tables of level 6 (sharing 128), on the 128-wavelength
+    // oblate spheroid the 3.5 GB tables of level 5 (sharing 30), save more time in the propagation
+    // and in the marking of relevant cones than they take to build.
     int64_t cap = (int64_t)1 << 30;
-    if (sharing >= 64.0) {
+    if (sharing >= 16.0) {
         size_t free_b = 0, total_b = 0;
         IFGF_CUDA(cudaMemGetInfo(&free_b, &total_b));
         cap = std::max(cap, std::min((int64_t)48 << 30, (int64_t)((free_b + pool_cached_bytes(p.device)) / 4)));
