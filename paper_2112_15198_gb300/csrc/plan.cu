@@ -489,78 +489,84 @@ __global__ void k_gamma_chunk_fill(int64_t n, const int32_t* __restrict__ flags,
     if (i == n - 1) gchunk[pos[i] + flags[i]] = (int32_t)n;  // end of the last chunk
 }
 
-// Activation from the nodes of the relevant parent cones, one block per chunk: the child cone of
-// node n seen from child octant o is classified once for the chunk (it depends on (gamma, o, n)
-// only) and marked in every child at octant o of the chunk's boxes.
-__global__ void __launch_bounds__(32 * kChunkBoxes)
-k_mark_parent_nodes_chunk(const int32_t* __restrict__ gchunk, const int32_t* __restrict__ gorder,
+// Activation from the nodes of the relevant parent cones, one warp per chunk (kMarkWarps chunks
+// per block, no block-wide barrier): the child cone of node n seen from child octant o is
+// classified once for the chunk (it depends on (gamma, o, n) only), for the octants that some box
+// of the chunk has a child at, and marked in every child at octant o of the chunk's boxes.
+constexpr int kMarkWarps = 8;
+__global__ void __launch_bounds__(32 * kMarkWarps, 6)
+k_mark_parent_nodes_chunk(const int32_t* __restrict__ gchunk, int64_t nchunk, const int32_t* __restrict__ gorder,
                           const int32_t* __restrict__ pcone_box, const int32_t* __restrict__ pcone_gam,
                           const int4* __restrict__ kp, const int32_t* __restrict__ pcstart,
                           const int4* __restrict__ kd, int D, int d, LevelGrid gp, LevelGrid g, ConeMark mark) {
     constexpr int Ps = 3, Pt = 5, Pp = 5, P = 75;
-    __shared__ int s_alpha[8][P];
-    __shared__ int s_omask;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int c0 = gchunk[blockIdx.x], nb = gchunk[blockIdx.x + 1] - c0;
-    if (tid == 0) s_omask = 0;
-    __syncthreads();
+    __shared__ int s_alpha_w[kMarkWarps][8][P];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * kMarkWarps + warp;
+    if (c >= nchunk) return;  // the whole warp leaves; nothing below synchronises the block
+    int(*s_alpha)[P] = s_alpha_w[warp];
+    const int c0 = gchunk[c], nb = gchunk[c + 1] - c0;  // nb <= kChunkBoxes
     const int gam = pcone_gam[gorder[c0]];
-    int jb = -1, k0 = 0, nch = 0;
-    int4 kj = make_int4(0, 0, 0, 0);
-    if (warp < nb) {
-        jb = pcone_box[gorder[c0 + warp]];
-        k0 = pcstart[jb];
-        nch = pcstart[jb + 1] - k0;
-        kj = kp[jb];
-        if (lane < nch) {
-            const int4 kk = kd[k0 + lane];
-            atomicOr(&s_omask, 1 << ((kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2)));
+    // octants with a child in some box of the chunk: lane x takes child x & 7 of box x >> 3
+    int om = 0;
+    for (int x = lane; x < 8 * nb; x += 32) {
+        const int jb = pcone_box[gorder[c0 + (x >> 3)]];
+        const int kb = pcstart[jb] + (x & 7);
+        if (kb < pcstart[jb + 1]) {
+            const int4 kj = kp[jb], kk = kd[kb];
+            om |= 1 << ((kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2));
         }
     }
-    __syncthreads();
-    const int om = s_omask, sh = D - d;
-    for (int x = tid; x < 8 * P; x += 32 * kChunkBoxes) {
-        const int o = x / P, n = x - (x / P) * P;
-        if (!((om >> o) & 1)) continue;
+    om = __reduce_or_sync(0xffffffffu, om);
+    const int sh = D - d;
+    for (int x = lane; x < __popc(om) * P; x += 32) {
+        const int oi = x / P, n = x - oi * P;
+        unsigned m = (unsigned)om;  // the oi-th octant present (oi < popc(om), so m stays nonzero)
+        for (int i = 0; i < oi; ++i) m &= m - 1;
+        const int o = __ffs(m) - 1;
         const float3 q = node_grid(gp, Ps, Pt, Pp, gam, n);
         const float ox = (float)((2 * (o & 1) - 1) << sh);
         const float oy = (float)((2 * ((o >> 1) & 1) - 1) << sh);
         const float oz = (float)((2 * ((o >> 2) & 1) - 1) << sh);
         s_alpha[o][n] = classify_f32(g, __fsub_rn(q.x, ox), __fsub_rn(q.y, oy), __fsub_rn(q.z, oz));
     }
-    __syncthreads();
-    if (warp >= nb) return;
-    for (int ch = 0; ch < nch; ++ch) {
-        const int4 kk = kd[k0 + ch];
-        const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
-        // the 75 nodes fall in a few child cones: collect the distinct ones over all nodes (lane g
-        // keeps the g-th), then mark each once
-        int a[3];
-        bool pend[3];
+    __syncwarp();
+    for (int b = 0; b < nb; ++b) {
+        const int jb = pcone_box[gorder[c0 + b]];
+        const int k0 = pcstart[jb], nch = pcstart[jb + 1] - k0;
+        const int4 kj = kp[jb];
+        for (int ch = 0; ch < nch; ++ch) {
+            const int4 kk = kd[k0 + ch];
+            const int o = (kk.x - 2 * kj.x) | ((kk.y - 2 * kj.y) << 1) | ((kk.z - 2 * kj.z) << 2);
+            // the 75 nodes fall in a few child cones: collect the distinct ones over all nodes (lane
+            // g keeps the g-th), then mark each once
+            int a[3];
+            bool pend[3];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int n = lane + 32 * j;
-            pend[j] = n < P;
-            a[j] = pend[j] ? s_alpha[o][n] : -1;
-        }
-        int mine = -1, G = 0;
-        for (int guard = 0; guard < P; ++guard) {
-            const unsigned b0 = __ballot_sync(0xffffffffu, pend[0]), b1 = __ballot_sync(0xffffffffu, pend[1]),
-                           b2 = __ballot_sync(0xffffffffu, pend[2]);
-            if (!(b0 | b1 | b2)) break;
-            const int sj = b0 ? 0 : (b1 ? 1 : 2);
-            const int src = __ffs(b0 ? b0 : (b1 ? b1 : b2)) - 1;
-            const int v = __shfl_sync(0xffffffffu, sj == 0 ? a[0] : (sj == 1 ? a[1] : a[2]), src);
-            if (lane == (G & 31)) mine = v;
-            if ((G & 31) == 31) {  // 32 distinct cones collected: mark them before collecting more
-                mark.mark(k0 + ch, mine);
-                mine = -1;
+            for (int j = 0; j < 3; ++j) {
+                const int n = lane + 32 * j;
+                pend[j] = n < P;
+                a[j] = pend[j] ? s_alpha[o][n] : -1;
             }
-            ++G;
+            int mine = -1, G = 0;
+            for (int guard = 0; guard < P; ++guard) {
+                const unsigned b0 = __ballot_sync(0xffffffffu, pend[0]), b1 = __ballot_sync(0xffffffffu, pend[1]),
+                               b2 = __ballot_sync(0xffffffffu, pend[2]);
+                if (!(b0 | b1 | b2)) break;
+                const int sj = b0 ? 0 : (b1 ? 1 : 2);
+                const int src = __ffs(b0 ? b0 : (b1 ? b1 : b2)) - 1;
+                const int v = __shfl_sync(0xffffffffu, sj == 0 ? a[0] : (sj == 1 ? a[1] : a[2]), src);
+                if (lane == (G & 31)) mine = v;
+                if ((G & 31) == 31) {  // 32 distinct cones collected: mark them before collecting more
+                    mark.mark(k0 + ch, mine);
+                    mine = -1;
+                }
+                ++G;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) pend[j] = pend[j] && a[j] != v;
+                for (int j = 0; j < 3; ++j) pend[j] = pend[j] && a[j] != v;
+            }
+            if (mine >= 0) mark.mark(k0 + ch, mine);
         }
-        if (mine >= 0) mark.mark(k0 + ch, mine);
     }
 }
 
@@ -1124,8 +1130,8 @@ void build_plan(Plan& p, const double* X, const ifgf_options& opt, int levels) {
                     IFGF_LAUNCH(k_mark_parent_nodes_tab, grid_for(Lp.nc * 8, kThreads), kThreads, 0, s, Lp.nc,
                                 Lp.cone_box, Lp.cone_gidx, Lp.k, Lp.cstart, L.k, Lp.tab_k, Lp.tab_list, cm);
                 else if (Lp.nc > 0 && Lp.n_gchunk > 0)
-                    IFGF_LAUNCH(k_mark_parent_nodes_chunk, (unsigned)Lp.n_gchunk, 32 * kChunkBoxes, 0, s, Lp.gchunk,
-                                Lp.gorder, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, D, d, Lp.g, L.g, cm);
+                    IFGF_LAUNCH(k_mark_parent_nodes_chunk, (unsigned)((Lp.n_gchunk + kMarkWarps - 1) / kMarkWarps),
+                                32 * kMarkWarps, 0, s, Lp.gchunk, (int64_t)Lp.n_gchunk, Lp.gorder, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, D, d, Lp.g, L.g, cm);
                 else if (Lp.nc > 0)
                     IFGF_LAUNCH(k_mark_parent_nodes, grid_for(Lp.nc * p.P, kThreads), kThreads, 0, s, Lp.nc, p.P, p.Ps,
                                 p.Pt, p.Pp, D, d, Lp.cone_box, Lp.cone_gam, Lp.k, Lp.cstart, L.k, Lp.g, L.g, cm);
