@@ -501,12 +501,19 @@ k_mark_parent_nodes_chunk(const int32_t* __restrict__ gchunk, int64_t nchunk, co
                           const int4* __restrict__ kd, int D, int d, LevelGrid gp, LevelGrid g, ConeMark mark) {
     constexpr int Ps = 3, Pt = 5, Pp = 5, P = 75;
     __shared__ int s_alpha_w[kMarkWarps][8][P];
+    __shared__ float4 s_q_w[kMarkWarps][P];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * kMarkWarps + warp;
     if (c >= nchunk) return;  // the whole warp leaves; nothing below synchronises the block
     int(*s_alpha)[P] = s_alpha_w[warp];
+    float4* s_q = s_q_w[warp];
     const int c0 = gchunk[c], nb = gchunk[c + 1] - c0;  // nb <= kChunkBoxes
     const int gam = pcone_gam[gorder[c0]];
+    // the cone's node offsets from the box centre (grid units), once for all octants
+    for (int n = lane; n < P; n += 32) {
+        const float3 q = node_grid(gp, Ps, Pt, Pp, gam, n);
+        s_q[n] = make_float4(q.x, q.y, q.z, 0.f);
+    }
     // octants with a child in some box of the chunk: lane x takes child x & 7 of box x >> 3
     int om = 0;
     for (int x = lane; x < 8 * nb; x += 32) {
@@ -518,13 +525,14 @@ k_mark_parent_nodes_chunk(const int32_t* __restrict__ gchunk, int64_t nchunk, co
         }
     }
     om = __reduce_or_sync(0xffffffffu, om);
+    __syncwarp();  // the node offsets are visible to the whole warp
     const int sh = D - d;
     for (int x = lane; x < __popc(om) * P; x += 32) {
         const int oi = x / P, n = x - oi * P;
         unsigned m = (unsigned)om;  // the oi-th octant present (oi < popc(om), so m stays nonzero)
         for (int i = 0; i < oi; ++i) m &= m - 1;
         const int o = __ffs(m) - 1;
-        const float3 q = node_grid(gp, Ps, Pt, Pp, gam, n);
+        const float4 q = s_q[n];
         const float ox = (float)((2 * (o & 1) - 1) << sh);
         const float oy = (float)((2 * ((o >> 1) & 1) - 1) << sh);
         const float oz = (float)((2 * ((o >> 2) & 1) - 1) << sh);
