@@ -490,6 +490,7 @@ __device__ __forceinline__ void prop_cone_warp_f32(WS* wp, int64_t ncp, const in
                                        : cm.find(k0 + ch, __ldg(&tab_list[(int64_t)s_row[ch] * kTabList + kl]));
         float ts[R], tt[R], tp[R];
         float2 ratio[R], F[R];
+        int node[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int64_t e = rowP + j0 + min(q, len - 1);  // short segments repeat their last node
@@ -497,6 +498,7 @@ __device__ __forceinline__ void prop_cone_warp_f32(WS* wp, int64_t ncp, const in
             ts[q] = t4.x;
             tt[q] = t4.y;
             tp[q] = t4.z;
+            node[q] = __float_as_int(t4.w);
             ratio[q] = __ldg(&tab_r[e]);
         }
         if (sv <= -2) {
@@ -511,7 +513,7 @@ __device__ __forceinline__ void prop_cone_warp_f32(WS* wp, int64_t ncp, const in
         }
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (q < len) vals[ch][__ldg(&tab_perm[rowP + j0 + q])] = cmul(F[q], ratio[q]);
+            if (q < len && (!kChecks || (unsigned)node[q] < (unsigned)P)) vals[ch][node[q]] = cmul(F[q], ratio[q]);
     }
     __syncwarp();
     for (int n = lane; n < P; n += 32) {  // sum over children, in child order

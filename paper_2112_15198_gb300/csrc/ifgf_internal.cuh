@@ -160,7 +160,7 @@ struct Level {
     int32_t* gam_list = nullptr;   // [n_gam] gamma of each row
     int32_t* cone_gidx = nullptr;  // [nc] row of each relevant cone
     // Entries of a row are stored in the order of their child cone (stable in the node index).
-    float4* tab_t = nullptr;       // (t_s, t_theta, t_phi, position of the child cone in the row's list)
+    float4* tab_t = nullptr;       // (t_s, t_theta, t_phi, node index in the parent cone)
     float2* tab_r = nullptr;       // G(x, x_k) / G(x, x_j)
     int32_t* tab_k = nullptr;      // [n_gam*8] distinct child cones of the row (K <= kTabList)
     int32_t* tab_list = nullptr;   // [n_gam*8][kTabList] their child cone indices

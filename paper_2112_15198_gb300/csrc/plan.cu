@@ -369,8 +369,8 @@ __global__ void k_node_tables(int64_t total, const int32_t* __restrict__ gam_lis
     tab_r[e] = make_float2(ex.x * w, ex.y * w);
 }
 
-// Distinct child cones of each table row (gamma, octant): the list, and each node's position in
-// it (replacing the cone index in tab_t.w).  Rows are built from the 75-node classification, so
+// Distinct child cones of each table row (gamma, octant): the list, and the row's entries sorted
+// by their position in it, with the node index in tab_t.w (replacing the cone index).  Rows are built from the 75-node classification, so
 // K <= 75 <= kTabList; a row past kTabList would make the build drop the level's tables.
 __global__ void k_node_lists(int P, float4* __restrict__ tab_t, float2* __restrict__ tab_r,
                              int32_t* __restrict__ tab_k, int32_t* __restrict__ tab_list,
@@ -426,7 +426,7 @@ __global__ void k_node_lists(int P, float4* __restrict__ tab_t, float2* __restri
             cnt += kpos[m] == k;
         }
         t = tab_t[row * P + n];
-        t.w = __int_as_float(k);
+        t.w = __int_as_float(n);  // node index in the parent cone (as tab_perm)
         rr = tab_r[row * P + n];
         segst[pos] = (pos - before) % kSegLen == 0;
     }
