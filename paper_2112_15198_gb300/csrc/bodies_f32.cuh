@@ -442,18 +442,18 @@ __device__ __forceinline__ void prop_cone_warp_f32(WS* wp, int64_t ncp, const in
     }
     if (lane == 0) s_goff[0] = s_koff[0] = 0;
     __syncwarp();
-    // child-cone slots, one list entry per lane; the first kWarpStage distinct blocks (the
-    // children's lists are disjoint) are copied to shared memory with coalesced asynchronous
-    // copies, the rest are read from global memory
-    for (int ch = 0; ch < nch; ++ch) {
-        const int row = s_row[ch];
-        const int Kc = s_koff[ch + 1] - s_koff[ch];
-        const int a = __ldg(&tab_list[(int64_t)row * kTabList + lane]);
-        if (lane < Kc && lane < kSlotCache) {
-            const int sl = cm.find(k0 + ch, a);
-            const int j = s_koff[ch] + lane;
+    // child-cone slots: distinct block j = koff[ch] + kl (list entry kl of child ch; the
+    // children's lists are disjoint), one block per lane over all children at once; the first
+    // kWarpStage blocks are copied to shared memory with coalesced asynchronous copies, the rest
+    // are read from global memory
+    for (int j = lane; j < s_koff[nch]; j += 32) {
+        int ch = 0;
+        while (ch + 1 < nch && s_koff[ch + 1] <= j) ++ch;
+        const int kl = j - s_koff[ch];
+        if (kl < kSlotCache) {
+            const int sl = cm.find(k0 + ch, __ldg(&tab_list[(int64_t)s_row[ch] * kTabList + kl]));
             const bool staged = sl >= 0 && j < kWarpStage;
-            s_slot[ch][lane] = staged ? -2 - j : sl;
+            s_slot[ch][kl] = staged ? -2 - j : sl;
             if (j < kWarpStage) s_dsl[j] = sl;
         }
     }
@@ -477,9 +477,9 @@ __device__ __forceinline__ void prop_cone_warp_f32(WS* wp, int64_t ncp, const in
     asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
     __syncwarp();
     const int total = 2 * s_goff[nch];
+    int ch = 0;  // a lane's items only move forward over the children
     for (int item = lane; item < total; item += 32) {
         const int seg = item >> 1, half = item & 1;
-        int ch = 0;
         while (ch + 1 < nch && s_goff[ch + 1] <= seg) ++ch;
         const int64_t rowP = (int64_t)s_row[ch] * P;
         const int sg = __ldg(&tab_seg[rowP + (seg - s_goff[ch])]);
