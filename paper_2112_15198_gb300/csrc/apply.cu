@@ -539,14 +539,29 @@ k_prop_mma_tab(int64_t ncp, const int32_t* __restrict__ pcone_box, const int32_t
     const int4 kj = kp[jb];
     const int dens = rhs0 + 8 * warp + g;  // density of A rows g / g + 8
     const int dl = 8 * warp + g;           // its row in f
-    for (int kb = pcstart[jb]; kb < pcstart[jb + 1]; ++kb) {
-        const int4 kk4 = kd[kb];
+    const int kb0 = pcstart[jb], nch = pcstart[jb + 1] - kb0;
+    // the children's rows, then the slots of their child cones (list positions below
+    // kSlotCache), looked up by the whole block at once before the products
+    __shared__ int s_row[8], s_K[8], s_sl[8][kSlotCache];
+    if (tid < nch) {
+        const int4 kk4 = kd[kb0 + tid];
         const int row = g8 + ((kk4.x - 2 * kj.x) | ((kk4.y - 2 * kj.y) << 1) | ((kk4.z - 2 * kj.z) << 2));
+        s_row[tid] = row;
+        s_K[tid] = __ldg(&tab_k[row]);
+    }
+    __syncthreads();
+    for (int x = tid; x < nch * kSlotCache; x += NTHR) {
+        const int ch = x / kSlotCache, kl = x - ch * kSlotCache;
+        if (kl < s_K[ch]) s_sl[ch][kl] = cm.find(kb0 + ch, __ldg(&tab_list[(int64_t)s_row[ch] * kTabList + kl]));
+    }
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
+        const int kb = kb0 + ch;
+        const int row = s_row[ch];
         const int64_t rowP = (int64_t)row * P;
-        const int K = __ldg(&tab_k[row]);
+        const int K = s_K[ch];
         for (int kl = 0; kl < K; ++kl) {
-            const int alpha = __ldg(&tab_list[(int64_t)row * kTabList + kl]);
-            const int sl = cm.find(kb, alpha);
+            const int sl = kl < kSlotCache ? s_sl[ch][kl] : cm.find(kb, __ldg(&tab_list[(int64_t)row * kTabList + kl]));
             if (sl < 0) set_status(status, IFGF_ERR_INTERNAL);
             const float2* blk = (sl >= 0 && dens < nrhs) ? cchild + ((int64_t)sl * nrhs + dens) * cstride : nullptr;
             uint32_t ah[10][4], al[10][4];
