@@ -513,7 +513,7 @@ __device__ __forceinline__ void prop_cone_warp_f32(WS* wp, int64_t ncp, const in
         }
 #pragma unroll
         for (int q = 0; q < R; ++q)
-            if (q < len && (!kChecks || (unsigned)node[q] < (unsigned)P)) vals[ch][node[q]] = cmul(F[q], ratio[q]);
+            if (q < len && in_bounds(node[q], P, status)) vals[ch][node[q]] = cmul(F[q], ratio[q]);
     }
     __syncwarp();
     for (int n = lane; n < P; n += 32) {  // sum over children, in child order
